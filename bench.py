@@ -1,0 +1,339 @@
+"""Throughput of the D3Q19 TRT sweep on GB300, in MFLUP/s (million fluid
+lattice-node updates per second) and as a fraction of the HBM roofline.
+
+Default workload: the 256^3 duct (bounce-back walls on four sides, periodic
+along x), FP64 PDFs, in-place AA propagation, seeded |u| <= 0.01 initial field,
+omega = 1, Lambda = 3/16. One "step" is one time step of the whole lattice.
+The lattice (2.55 GB) is far larger than L2 (129 MB), so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line. --impl reference times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1711_11468_gb300 import inputs  # noqa: E402
+
+WORKLOAD = inputs.DUCT_256
+DIMS = WORKLOAD["dims"]
+METRIC = "MFLUP/s and % of HBM roofline, FP64 vs FP32/FP16-shifted vs batched, at stated error"
+UNIT = "MFLUP/s"
+
+# Loop balance per fluid lattice update on a GPU (no write-allocate): 19 loads
+# and 19 stores of S bytes, plus the int32 adjacency for the fluid list
+# (18 entries every step for pull, every other step for AA).
+def bytes_per_flup(elem_bytes: int, indirect: bool, propagation: str) -> float:
+    b = 2 * 19 * elem_bytes
+    if indirect:
+        b += 72 if propagation == "pull" else 36
+    return float(b)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("LBM_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- GPU arm
+def make_duct(lbm, stream, precision, propagation, host_u=None):
+    desc = lbm.make_desc(DIMS, precision, lbm.LBM_DIRECT, propagation, periodic=(1, 0, 0))
+    h = lbm.lbm_create_lattice(desc, stream)
+    flags = inputs.duct_flags(*DIMS)
+    lbm.lbm_set_geometry(h, 0, flags)
+    lbm.lbm_set_params(h, 0, WORKLOAD["omega"], WORKLOAD["Lambda"], WORKLOAD["force"])
+    if host_u is None:
+        host_u = inputs.velocity_perturbation(*DIMS, seed=WORKLOAD["seed"], amplitude=WORKLOAD["amplitude"],
+                                              flags=flags)
+    lbm.lbm_init_equilibrium(h, 0, None, host_u)
+    return h, flags
+
+
+def time_steps(lbm, h, steps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lbm.lbm_step(h, steps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def variant(lbm, stream, precision, propagation, steps, nf, peak):
+    h, _ = make_duct(lbm, stream, precision, propagation)
+    try:
+        lbm.lbm_step(h, 4)
+        sec = time_steps(lbm, h, steps, stream)
+    finally:
+        lbm.lbm_destroy(h)
+    mflups = nf * steps / sec / 1e6
+    elem = {lbm.LBM_F64: 8, lbm.LBM_F32_SHIFTED: 4, lbm.LBM_F16_SHIFTED: 2}[precision]
+    bpf = bytes_per_flup(elem, False, "pull" if propagation == lbm.LBM_PULL_TWO_GRID else "aa")
+    gbs = mflups * 1e6 * bpf / 1e9
+    return {"mflups": round(mflups, 1), "bytes_per_flup": bpf, "achieved_gbs": round(gbs, 1),
+            "roofline_frac": round(gbs / peak, 4), "steps": steps}
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_1711_11468_gb300 import lbm
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    lbm.load()
+    lbm.use_torch_allocator()
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = measured_peaks()
+
+    h, flags = make_duct(lbm, stream, lbm.LBM_F64, lbm.LBM_AA_INPLACE)
+    nf = int(np.count_nonzero(flags == 0))
+    lbm.lbm_step(h, args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    sec = time_steps(lbm, h, args.steps, stream)
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sec_max = max_over_ranks(sec, world, f"cuda:{local}")
+    moments = lbm.lbm_read_moments(h, 0)
+    lbm.lbm_destroy(h)
+
+    value = nf * args.steps * world / sec_max / 1e6
+    bpf = bytes_per_flup(8, False, "aa")
+    achieved = value / world * 1e6 * bpf / 1e9
+
+    # end to end through the C ABI from host buffers: geometry + initial field
+    # up, K steps, density and velocity back
+    host_u = inputs.velocity_perturbation(*DIMS, seed=WORKLOAD["seed"], amplitude=WORKLOAD["amplitude"],
+                                          flags=flags)
+    N = flags.size
+    rho_out, u_out = np.empty(N), np.empty((3, N))
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h2, _ = make_duct(lbm, stream, lbm.LBM_F64, lbm.LBM_AA_INPLACE, host_u=host_u)
+    lbm.lbm_step(h2, args.steps)
+    lbm.lbm_read_macroscopic(h2, 0, rho_out, u_out)
+    e2e_sec = time.perf_counter() - t0
+    lbm.lbm_destroy(h2)
+    e2e_sec = max_over_ranks(e2e_sec, world, f"cuda:{local}")
+    e2e_value = nf * args.steps * world / e2e_sec / 1e6
+
+    variants = {}
+    if rank == 0 and not args.no_variants:
+        vs = min(args.steps, 200)
+        variants["f64_pull_two_grid"] = variant(lbm, stream, lbm.LBM_F64, lbm.LBM_PULL_TWO_GRID, vs, nf, peak)
+        variants["f32_shifted_aa"] = variant(lbm, stream, lbm.LBM_F32_SHIFTED, lbm.LBM_AA_INPLACE, vs, nf, peak)
+        variants["f16_shifted_aa"] = variant(lbm, stream, lbm.LBM_F16_SHIFTED, lbm.LBM_AA_INPLACE, vs, nf, peak)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(sec_max * 1e3 / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded |u|<=0.01 equilibrium field)",
+            "config": {"workload": "D3Q19 TRT duct 256^3, FP64 PDFs, direct addressing, SoA, in-place AA, "
+                                   "full-way bounce-back walls on y and z, periodic x",
+                       "dims": list(DIMS), "fluid_cells": nf, "omega": WORKLOAD["omega"],
+                       "Lambda": WORKLOAD["Lambda"], "l2": "inputs larger than L2 (2.55 GB lattice)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "bytes_per_flup": bpf, "peak_source": peak_kind},
+            "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
+                    "h2d_bytes_per_step": (N + 3 * N * 8) / args.steps,
+                    "d2h_bytes_per_step": 4 * N * 8 / args.steps},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "mass_after": moments[0],
+            "variants": variants,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ CPU oracle arm
+def cpu_sample(seconds: float):
+    """Oracle push steps on the duct workload until `seconds` of CPU work."""
+    import oracle
+    oracle.build()
+    flags = inputs.duct_flags(*DIMS)
+    nf = int(np.count_nonzero(flags == 0))
+    u = inputs.velocity_perturbation(*DIMS, seed=WORKLOAD["seed"], amplitude=WORKLOAD["amplitude"], flags=flags)
+    f = oracle.init_equilibrium(DIMS, flags, None, u)
+    g = np.zeros_like(f)
+    wm = oracle.omega_minus(WORKLOAD["omega"], WORKLOAD["Lambda"])
+    steps, t = 0, 0.0
+    while t < seconds or steps == 0:
+        t0 = time.perf_counter()
+        oracle.step(DIMS, flags, WORKLOAD["omega"], wm, WORKLOAD["force"], f, g)
+        t += time.perf_counter() - t0
+        f, g = g, f
+        steps += 1
+    return nf * steps / t / 1e6, steps, t, oracle.max_threads()
+
+
+def cpu_baseline(seconds: float):
+    v, steps, t, cores = cpu_sample(seconds)
+    return {"value": round(v, 2), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} oracle steps of the 256^3 duct ({t:.1f} s, FP64 push, OpenMP)"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    v, steps, t, cores = cpu_sample(args.cpu_seconds)
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 2), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "D3Q19 TRT duct 256^3, FP64 CPU oracle (two-grid push)", "dims": list(DIMS)},
+            "cpu_baseline": {"value": round(v, 2), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{steps} oracle steps of the 256^3 duct ({t:.1f} s)"},
+            "e2e": {"value": round(v, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * lbm_gb300.h -- C ABI of the GB300 (sm_103a) D3Q19 TRT lattice Boltzmann sweep.
+ *
+ * The method is the fused collide-and-propagate sweep of Wittmann et al.,
+ * "Lattice Boltzmann Benchmark Kernels as a Testbed for Performance Analysis"
+ * (arXiv 1711.11468): D3Q19 velocities with the two-relaxation-time (TRT)
+ * collision (Sec. 2), half-way or full-way bounce-back (Sec. 2, Sec. 3.2),
+ * full-array (direct) or fluid-list (indirect, adjacency list) addressing
+ * (Sec. 3 "Lattice Representation"), structure-of-arrays layout (Sec. 3 "Data
+ * Layout"), and two-grid one-step pull or in-place AA-pattern propagation
+ * (Sec. 3 "One Step Kernels", "AA Pattern Kernels"). The body force is the
+ * paper's verification set-up (Sec. 2.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns an lbm_status. Nothing throws or aborts across the ABI.
+ *    lbm_last_error() gives a thread-local message for the last failure.
+ *  - Host pointers are owned by the caller and are only read or written during
+ *    the call. Device memory is owned by the library: it is allocated through
+ *    the hook set by lbm_set_allocator (default: cudaMalloc/cudaFree) and freed
+ *    by lbm_destroy.
+ *  - Work is issued on the CUDA stream given at creation (NULL = the legacy
+ *    default stream). lbm_step is asynchronous; every lbm_read_* call and
+ *    lbm_synchronize wait for that stream before returning.
+ *  - A CUDA error observed by any call poisons the handle: that call and every
+ *    later one on the handle return LBM_ERR_CUDA.
+ *  - Order: create -> set_geometry -> set_params -> init_equilibrium (or
+ *    write_pdfs) -> step / read. Out-of-order calls return LBM_ERR_STATE.
+ *
+ * Lattice conventions
+ * -------------------
+ *  - Cell index n = x + nx*(y + ny*z), x fastest; N = nx*ny*nz.
+ *  - Direction order i = 0..18 (every array indexed by direction uses it):
+ *      0 rest; 1..9 = (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,-1,0) (1,0,1)
+ *      (1,0,-1) (0,1,1) (0,1,-1); 10..18 = the negatives of 1..9, so the
+ *      opposite of i is i+9 for 1<=i<=9. Weights 1/3, 1/18 (faces), 1/36 (edges).
+ *  - Flags (uint8 per cell): 0 fluid; 1 full-way bounce-back solid (holds PDFs
+ *    and reverses them instead of colliding; direct addressing only);
+ *    2 half-way bounce-back solid (holds nothing; a link into it reflects at
+ *    mid-link).
+ *  - Index arithmetic wraps in every dimension. A dimension whose periodic flag
+ *    is 0 must be closed by solid cells on both boundary layers, so that no
+ *    fluid population ever wraps; otherwise set_geometry returns LBM_ERR_ARG.
+ *  - Canonical PDFs are f_i(x, t): post-streaming, pre-collision, FP64, laid
+ *    out double[19][N]. Half-way solid cells read as 0. Reads and writes are
+ *    canonical whatever the storage precision, addressing or AA parity.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_lattice_s* lbm_handle;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = 1,          /* invalid argument (NULL, size, range, geometry) */
+  LBM_ERR_STATE = 2,        /* call out of order, or handle poisoned by misuse */
+  LBM_ERR_OOM = 3,          /* the allocator returned NULL */
+  LBM_ERR_CUDA = 4,         /* a CUDA call failed; the handle is poisoned */
+  LBM_ERR_UNSUPPORTED = 5,  /* valid request this build does not serve */
+  LBM_ERR_TIMEOUT = 6       /* reserved for bounded device-side waits */
+} lbm_status;
+
+/* PDF storage: FP64 values, or the deviation f_i - w_i from the rest state
+ * stored in FP32 / FP16 (round to nearest even) with FP32 collision arithmetic.
+ * The paper stores FP64 only (Sec. 2); the shifted formats are additions. */
+typedef enum { LBM_F64 = 0, LBM_F32_SHIFTED = 1, LBM_F16_SHIFTED = 2 } lbm_precision;
+
+/* Full array with flag field (direct) or fluid list + int32 adjacency list
+ * with 18 neighbours per node (indirect), Sec. 3 "Lattice Representation". */
+typedef enum { LBM_DIRECT = 0, LBM_INDIRECT = 1 } lbm_addressing;
+
+/* One-step pull with two grids (Sec. 3 "One Step Kernels") or the AA pattern
+ * on one grid, alternating a node-local even step and a neighbour-accessing
+ * odd step (Sec. 3 "AA Pattern Kernels"). */
+typedef enum { LBM_PULL_TWO_GRID = 0, LBM_AA_INPLACE = 1 } lbm_propagation;
+
+typedef struct {
+  int32_t nx, ny, nz;     /* each >= 2 */
+  uint8_t periodic[3];    /* 1 = periodic; 0 = closed by solid layers (see above) */
+  uint8_t reserved;       /* must be 0 */
+  int32_t precision;      /* lbm_precision */
+  int32_t addressing;     /* lbm_addressing */
+  int32_t propagation;    /* lbm_propagation */
+} lbm_desc;
+
+/* Device allocator hook, process-wide, used by handles created afterwards.
+ * alloc(bytes, ctx) returns a device pointer or NULL; free_(ptr, ctx).
+ * Passing alloc == free_ == NULL restores cudaMalloc/cudaFree. */
+typedef void* (*lbm_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*lbm_free_fn)(void* ptr, void* ctx);
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_, void* ctx);
+
+/* Create one lattice (Sec. 3: representation, layout and propagation chosen
+ * per kernel, Table 1). cuda_stream is a cudaStream_t or NULL. Allocates the
+ * flag field now; PDF storage is allocated by set_geometry (its size depends on
+ * the fluid count for indirect addressing). *out receives the handle. */
+int lbm_create_lattice(const lbm_desc* desc, void* cuda_stream, lbm_handle* out);
+
+/* Create a batch of `count` independent lattices (1 <= count <= 65536) that
+ * advance together: every lbm_step is one launch per time step covering all
+ * of them (a work list of tiles over all lattices). All descriptors must share
+ * precision and propagation; addressing may differ per lattice. Lattice k of a
+ * batch is addressed by `lattice` = k in the calls below. Not in the paper. */
+int lbm_create_batch(const lbm_desc* descs, int32_t count, void* cuda_stream, lbm_handle* out);
+
+/* Set the geometry of lattice `lattice` from host flags uint8[N] (values 0, 1
+ * or 2; 1 is rejected for indirect addressing, which stores fluid cells only).
+ * Builds, on the device, the fluid list in lexicographic order and the
+ * adjacency list (indirect), and allocates PDF storage. Synchronous. */
+int lbm_set_geometry(lbm_handle h, int32_t lattice, const uint8_t* flags);
+
+/* Set the geometry to fluid everywhere except the cells inside the given
+ * spheres, which become half-way solid (flag 2). cxyzr is int32[4*nspheres]:
+ * centre x, y, z and radius r >= 0; a cell is inside when
+ * dx^2 + dy^2 + dz^2 <= r^2 with minimum-image periodic offsets. The
+ * voxelisation runs on the device (the paper's heterogeneous geometries,
+ * Sec. 2 and Sec. 4.5, realised as a porous medium). Synchronous. */
+int lbm_set_geometry_spheres(lbm_handle h, int32_t lattice, const int32_t* cxyzr, int32_t nspheres);
+
+/* TRT parameters (Sec. 2): omega in (0, 2) is omega+ (viscosity
+ * nu = (1/omega - 1/2)/3); Lambda > 0 is the magic parameter
+ * (1/omega+ - 1/2)(1/omega- - 1/2); force[3] is the constant body force of the
+ * verification set-up (Sec. 2.1), applied on every fluid node as the source
+ * 3 w_i (c_i . F) after collision. lattice = -1 sets every lattice. */
+int lbm_set_params(lbm_handle h, int32_t lattice, double omega, double Lambda, const double force[3]);
+
+/* Initial state f_i(x, 0) = equilibrium(rho(x), u(x)) at fluid and full-way
+ * solid cells; rho double[N] or NULL (1), u double[3][N] or NULL (0). The
+ * equilibrium is the second-order w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u).
+ * Resets the step counter to 0. Synchronous. */
+int lbm_init_equilibrium(lbm_handle h, int32_t lattice, const double* rho, const double* u);
+
+/* Advance every lattice of the handle by n >= 0 time steps (the fused
+ * collide-and-propagate sweep, Sec. 3). Asynchronous on the handle's stream;
+ * runs of steps are replayed from captured CUDA graphs. */
+int lbm_step(lbm_handle h, int32_t n);
+
+/* Wait for all work issued on the handle's stream. */
+int lbm_synchronize(lbm_handle h);
+
+/* Steps taken since the last init_equilibrium / write_pdfs. */
+int lbm_steps_done(lbm_handle h, int64_t* steps);
+
+/* Canonical PDFs f_i(x, t) of one lattice into out double[19*N] (out_len is
+ * the element count, >= 19*N). Synchronous. */
+int lbm_read_pdfs(lbm_handle h, int32_t lattice, double* out, size_t out_len);
+
+/* Replace the state of one lattice by canonical PDFs in double[19*N]
+ * (checkpoint restore; values at half-way solid cells are ignored). Resets
+ * the step counter to 0. Synchronous. */
+int lbm_write_pdfs(lbm_handle h, int32_t lattice, const double* in, size_t in_len);
+
+/* Density rho double[N] and velocity u double[3][N] of one lattice, in FP64
+ * from the canonical PDFs: rho = sum f_i, u = (sum c_i f_i + F/2) / rho;
+ * 0 at solid cells. Either pointer may be NULL. Synchronous. */
+int lbm_read_macroscopic(lbm_handle h, int32_t lattice, double* rho, double* u);
+
+/* Mean of velocity component `comp` (0..2) over the fluid cells of every
+ * plane normal to `axis` (0..2), in FP64: out double[n_axis] (0 for planes
+ * without fluid). The velocity profile compared with the analytic Poiseuille
+ * solution in the verification set-up (Sec. 2.1). Synchronous. */
+int lbm_read_profile(lbm_handle h, int32_t lattice, int32_t axis, int32_t comp, double* out, size_t out_len);
+
+/* FP64 sums over every stored PDF of one lattice (fluid and full-way solid
+ * cells): out[0] = sum_x sum_i f_i (mass), out[1..3] = sum_x sum_i c_i f_i
+ * (momentum). Synchronous. */
+int lbm_read_moments(lbm_handle h, int32_t lattice, double out[4]);
+
+/* Flags uint8[N] of one lattice as the library holds them (for spheres: the
+ * device voxelisation). Synchronous. */
+int lbm_read_flags(lbm_handle h, int32_t lattice, uint8_t* out, size_t out_len);
+
+/* Number of fluid cells of one lattice. */
+int lbm_fluid_count(lbm_handle h, int32_t lattice, int64_t* n_fluid);
+
+/* Adjacency list of an indirectly addressed lattice into out int32[18*Nf],
+ * entry (i-1)*Nf + k for direction i = 1..18 and list node k: the list index
+ * of the upstream node x_k - c_i (wrapped) if fluid, else -1 (a bounce-back
+ * link). Nodes are the fluid cells in lexicographic order. Table 1's int32
+ * adjacency with 18 neighbours. LBM_ERR_ARG for a directly addressed lattice.
+ * Synchronous. */
+int lbm_read_adjacency(lbm_handle h, int32_t lattice, int32_t* out, size_t out_len);
+
+/* Kernel launch shape of the handle's sweep: threads per block and cells per
+ * thread (the batch also uses the tile size in cells). lbm_set_tuning fixes
+ * it (0 = keep); lbm_autotune times candidate shapes for `steps` steps each on
+ * the handle's own data (state is saved and restored around the trials) and
+ * keeps the fastest. Tuning is the launch-shape analogue of the paper's
+ * search over blocking factors (Sec. 4.2, Sec. 4.3). */
+int lbm_set_tuning(lbm_handle h, int32_t threads, int32_t cells_per_thread, int32_t tile_cells);
+int lbm_get_tuning(lbm_handle h, int32_t out[3]);
+int lbm_autotune(lbm_handle h, int32_t steps);
+
+/* Device bytes the handle holds (flags, PDF storage, fluid and adjacency
+ * lists, batch tables). */
+int lbm_memory_bytes(lbm_handle h, int64_t* bytes);
+
+int lbm_destroy(lbm_handle h);
+
+/* Thread-local message describing the last failed call ("" if none). */
+const char* lbm_last_error(void);
+
+/* ----------------------------------------------------------------------
+ * Bandwidth micro-benchmarks (Sec. 4.1): the GPU counterparts of the paper's
+ * copy-19 (19 arrays copied concurrently) and update-19 (19 arrays updated in
+ * place). Device pointers; arrays are `n` elements of `elem_bytes` (4 or 8)
+ * each, at src + k*stride_elems (k = 0..18). Asynchronous on cuda_stream.
+ * ---------------------------------------------------------------------- */
+int lbm_bench_copy19(const void* src, void* dst, int64_t n, int64_t stride_elems, int32_t elem_bytes,
+                     void* cuda_stream);
+int lbm_bench_update19(void* buf, int64_t n, int64_t stride_elems, int32_t elem_bytes, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,706 @@
+// The C ABI of liblbm_gb300.so (declared and documented in include/lbm_gb300.h):
+// handle lifecycle, device memory through the allocator hook, geometry set-up,
+// state conversion, the time loop (replayed from CUDA graphs) and readback.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+#include "lbm_model.cuh"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_error;
+
+std::mutex g_alloc_mu;
+lbm_alloc_fn g_alloc = nullptr;
+lbm_free_fn g_free = nullptr;
+void* g_alloc_ctx = nullptr;
+
+constexpr int kGraphSteps = 16;   // steps per captured graph (even: parity returns)
+
+int fail(int code, const std::string& msg) {
+  g_error = msg;
+  return code;
+}
+
+struct Lattice {
+  lbm_desc desc{};
+  int64_t N = 0, nf = 0, nstore = 0, stride = 0;
+  uint8_t* flags = nullptr;
+  void* pdf[2] = {nullptr, nullptr};
+  int32_t* adj = nullptr;
+  int32_t* cell_of = nullptr;
+  int32_t* list_index = nullptr;
+  bool has_halfway = false, has_fullway = false;
+  bool geometry = false, params = false, init = false;
+  double omega = 1.0, Lambda = 0.25;
+  TrtParams trt;
+
+  bool indirect() const { return desc.addressing == LBM_INDIRECT; }
+  LatticeView view() const {
+    LatticeView v;
+    v.nx = desc.nx;
+    v.ny = desc.ny;
+    v.nz = desc.nz;
+    v.n_cells = N;
+    v.n_nodes = nstore;
+    v.stride = stride;
+    v.prec = desc.precision;
+    v.indirect = indirect();
+    v.has_halfway = has_halfway;
+    v.flags = flags;
+    v.adj = adj;
+    v.cell_of = cell_of;
+    v.list_index = list_index;
+    return v;
+  }
+};
+
+}  // namespace
+
+struct lbm_lattice_s {
+  std::vector<Lattice> lat;
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  int prec = 0, prop = 0;
+  int64_t steps = 0;     // since the last init / write
+  int phase = 0;         // total steps mod 2: AA parity, pull buffer holding the state
+  bool poisoned = false;
+  int threads = 256, cells_per_thread = 1, tile_cells = 0;
+  lbm_alloc_fn alloc = nullptr;
+  lbm_free_fn free_ = nullptr;
+  void* alloc_ctx = nullptr;
+  int64_t bytes = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  void* dalloc(size_t n) {
+    if (n == 0) n = 256;
+    void* p = nullptr;
+    if (alloc) {
+      p = alloc(n, alloc_ctx);
+    } else if (cudaMalloc(&p, n) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (p) bytes += (int64_t)n;
+    return p;
+  }
+  void dfree(void* p, size_t n) {
+    if (!p) return;
+    if (n == 0) n = 256;
+    bytes -= (int64_t)n;
+    if (free_)
+      free_(p, alloc_ctx);
+    else
+      cudaFree(p);
+  }
+  void drop_graphs() {
+    for (auto& g : graph) {
+      if (g) cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  }
+};
+
+namespace {
+
+size_t pdf_bytes(const Lattice& L, int prec) { return (size_t)Q * (size_t)L.stride * (size_t)elem_bytes(prec); }
+
+int cuda_fail(lbm_handle h, cudaError_t e, const char* what) {
+  if (h) h->poisoned = true;
+  return fail(LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(h, expr, what)                        \
+  do {                                                 \
+    cudaError_t e_ = (expr);                           \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+  } while (0)
+
+int check_handle(lbm_handle h) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  if (h->poisoned) return fail(LBM_ERR_CUDA, "handle poisoned by an earlier CUDA error");
+  return LBM_OK;
+}
+
+int check_lattice(lbm_handle h, int32_t lattice) {
+  if (int rc = check_handle(h)) return rc;
+  if (lattice < 0 || lattice >= (int32_t)h->lat.size()) return fail(LBM_ERR_ARG, "lattice index out of range");
+  return LBM_OK;
+}
+
+int validate_desc(const lbm_desc* d) {
+  if (!d) return fail(LBM_ERR_ARG, "null descriptor");
+  if (d->nx < 2 || d->ny < 2 || d->nz < 2) return fail(LBM_ERR_ARG, "every dimension must be >= 2");
+  const int64_t N = (int64_t)d->nx * d->ny * d->nz;
+  if (N >= ((int64_t)1 << 31)) return fail(LBM_ERR_ARG, "lattice too large: N must be < 2^31 cells");
+  if (d->precision < LBM_F64 || d->precision > LBM_F16_SHIFTED) return fail(LBM_ERR_ARG, "bad precision");
+  if (d->addressing != LBM_DIRECT && d->addressing != LBM_INDIRECT) return fail(LBM_ERR_ARG, "bad addressing");
+  if (d->propagation != LBM_PULL_TWO_GRID && d->propagation != LBM_AA_INPLACE)
+    return fail(LBM_ERR_ARG, "bad propagation");
+  for (int a = 0; a < 3; ++a)
+    if (d->periodic[a] > 1) return fail(LBM_ERR_ARG, "periodic flags must be 0 or 1");
+  if (d->reserved != 0) return fail(LBM_ERR_ARG, "reserved field must be 0");
+  return LBM_OK;
+}
+
+Layout current_layout(const lbm_handle h) {
+  if (h->prop == LBM_PULL_TWO_GRID) return kPullForm;
+  return h->phase == 0 ? kCanonical : kAAForm;
+}
+
+void* state_buffer(lbm_handle h, Lattice& L) {
+  return h->prop == LBM_PULL_TWO_GRID ? L.pdf[h->phase] : L.pdf[0];
+}
+
+// RAII device scratch for one call, freed after the stream is drained.
+struct Scratch {
+  lbm_handle h;
+  void* p = nullptr;
+  size_t n = 0;
+  Scratch(lbm_handle h_, size_t n_) : h(h_), n(n_) { p = h->dalloc(n); }
+  ~Scratch() {
+    if (p) {
+      cudaStreamSynchronize(h->stream);
+      h->dfree(p, n);
+    }
+  }
+  template <typename T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+int create_impl(const lbm_desc* descs, int32_t count, void* stream, lbm_handle* out) {
+  if (!out) return fail(LBM_ERR_ARG, "null output handle");
+  *out = nullptr;
+  if (!descs || count < 1 || count > 65536) return fail(LBM_ERR_ARG, "count must be in [1, 65536]");
+  for (int32_t k = 0; k < count; ++k)
+    if (int rc = validate_desc(descs + k)) return rc;
+  for (int32_t k = 1; k < count; ++k)
+    if (descs[k].precision != descs[0].precision || descs[k].propagation != descs[0].propagation)
+      return fail(LBM_ERR_ARG, "all lattices of a batch must share precision and propagation");
+  lbm_handle h = new lbm_lattice_s();
+  {
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    h->alloc = g_alloc;
+    h->free_ = g_free;
+    h->alloc_ctx = g_alloc_ctx;
+  }
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->prec = descs[0].precision;
+  h->prop = descs[0].propagation;
+  h->lat.resize(count);
+  cudaError_t e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
+  if (e != cudaSuccess) {
+    lbm_destroy(h);
+    return fail(LBM_ERR_CUDA, std::string("stream/event creation: ") + cudaGetErrorString(e));
+  }
+  for (int32_t k = 0; k < count; ++k) {
+    Lattice& L = h->lat[k];
+    L.desc = descs[k];
+    L.N = (int64_t)L.desc.nx * L.desc.ny * L.desc.nz;
+    L.flags = static_cast<uint8_t*>(h->dalloc((size_t)L.N));
+    if (!L.flags) {
+      lbm_destroy(h);
+      return fail(LBM_ERR_OOM, "allocation of the flag field failed");
+    }
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+void free_storage(lbm_handle h, Lattice& L) {
+  const size_t pb = pdf_bytes(L, h->prec);
+  for (auto& p : L.pdf) {
+    h->dfree(p, pb);
+    p = nullptr;
+  }
+  h->dfree(L.adj, (size_t)18 * L.stride * sizeof(int32_t));
+  h->dfree(L.cell_of, (size_t)L.nf * sizeof(int32_t));
+  h->dfree(L.list_index, (size_t)L.N * sizeof(int32_t));
+  L.adj = L.cell_of = L.list_index = nullptr;
+}
+
+// Validate the flags now on the device, build lists and allocate storage.
+int finish_geometry(lbm_handle h, Lattice& L) {
+  h->drop_graphs();
+  L.geometry = L.init = false;
+  free_storage(h, L);
+  Scratch cnt(h, 10 * sizeof(unsigned long long));
+  if (!cnt.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
+  unsigned long long* d = cnt.as<unsigned long long>();
+  LBM_CUDA(h, cudaMemsetAsync(d, 0, 10 * sizeof(unsigned long long), h->stream), "memset");
+  LBM_CUDA(h, launch_count_flags(L.flags, L.N, d, h->stream), "count flags");
+  LBM_CUDA(h, launch_face_fluid(L.flags, L.desc.nx, L.desc.ny, L.desc.nz, d + 4, h->stream), "face check");
+  unsigned long long c[10];
+  LBM_CUDA(h, cudaMemcpyAsync(c, d, sizeof(c), cudaMemcpyDeviceToHost, h->stream), "copy counts");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "geometry sync");
+  if (c[3] != 0) return fail(LBM_ERR_ARG, "flags must be 0, 1 or 2");
+  if (L.indirect() && c[1] != 0)
+    return fail(LBM_ERR_ARG, "indirect addressing stores fluid cells only: full-way solid (flag 1) is not allowed");
+  for (int a = 0; a < 3; ++a)
+    if (!L.desc.periodic[a] && (c[4 + 2 * a] != 0 || c[5 + 2 * a] != 0))
+      return fail(LBM_ERR_ARG, "a non-periodic dimension must be closed by solid cells on both boundary layers");
+  L.nf = (int64_t)c[0];
+  L.has_fullway = c[1] != 0;
+  L.has_halfway = c[2] != 0;
+  L.nstore = L.indirect() ? L.nf : L.N;
+  L.stride = std::max<int64_t>(128, (L.nstore + 127) / 128 * 128);
+  const size_t pb = pdf_bytes(L, h->prec);
+  const int ngrids = h->prop == LBM_PULL_TWO_GRID ? 2 : 1;
+  for (int g = 0; g < ngrids; ++g) {
+    L.pdf[g] = h->dalloc(pb);
+    if (!L.pdf[g]) return fail(LBM_ERR_OOM, "allocation of PDF storage failed");
+    LBM_CUDA(h, cudaMemsetAsync(L.pdf[g], 0, pb, h->stream), "memset pdf");
+  }
+  if (L.indirect()) {
+    L.list_index = static_cast<int32_t*>(h->dalloc((size_t)L.N * sizeof(int32_t)));
+    L.cell_of = static_cast<int32_t*>(h->dalloc((size_t)L.nf * sizeof(int32_t)));
+    L.adj = static_cast<int32_t*>(h->dalloc((size_t)18 * L.stride * sizeof(int32_t)));
+    if (!L.list_index || !L.cell_of || !L.adj) return fail(LBM_ERR_OOM, "allocation of the adjacency list failed");
+    LBM_CUDA(h, cudaMemsetAsync(L.adj, 0xff, (size_t)18 * L.stride * sizeof(int32_t), h->stream), "memset adj");
+    Scratch tmp(h, (size_t)scan_tmp_elems(L.N) * sizeof(int32_t));
+    if (!tmp.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
+    Scratch nfbuf(h, sizeof(int64_t));
+    if (!nfbuf.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
+    LBM_CUDA(h, launch_compact(L.flags, L.N, L.list_index, L.cell_of, tmp.as<int32_t>(), nfbuf.as<int64_t>(),
+                               h->stream),
+             "compaction");
+    LatticeView v = L.view();
+    LBM_CUDA(h, launch_adjacency(v, L.list_index, L.adj, h->stream), "adjacency");
+    int64_t nf_check = -1;
+    LBM_CUDA(h, cudaMemcpyAsync(&nf_check, nfbuf.p, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream), "copy nf");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "adjacency sync");
+    if (nf_check != L.nf) return fail(LBM_ERR_STATE, "fluid compaction disagrees with the flag count");
+  }
+  L.geometry = true;
+  return LBM_OK;
+}
+
+void fill_trt(Lattice& L, double omega, double Lambda, const double F[3]) {
+  L.omega = omega;
+  L.Lambda = Lambda;
+  L.trt.omega_p = omega;
+  L.trt.omega_m = 1.0 / (Lambda / (1.0 / omega - 0.5) + 0.5);
+  for (int a = 0; a < 3; ++a) L.trt.force[a] = F[a];
+  for (int k = 1; k <= 9; ++k)
+    L.trt.fk[k - 1] = 3.0 * weight(k) * (cx(k) * F[0] + cy(k) * F[1] + cz(k) * F[2]);
+}
+
+int ready_to_step(lbm_handle h) {
+  for (size_t k = 0; k < h->lat.size(); ++k) {
+    const Lattice& L = h->lat[k];
+    if (!L.geometry || !L.params || !L.init)
+      return fail(LBM_ERR_STATE, "lattice " + std::to_string(k) + " needs geometry, params and an initial state");
+  }
+  return LBM_OK;
+}
+
+// Launch one time step of every lattice on stream s, at phase `phase`.
+cudaError_t issue_step(lbm_handle h, int phase, cudaStream_t s) {
+  for (Lattice& L : h->lat) {
+    const LatticeView v = L.view();
+    cudaError_t e;
+    if (h->prop == LBM_PULL_TWO_GRID)
+      e = launch_sweep(v, kPull, L.pdf[phase], L.pdf[phase ^ 1], L.trt, h->threads, s);
+    else
+      e = launch_sweep(v, phase == 0 ? kAAEven : kAAOdd, L.pdf[0], L.pdf[0], L.trt, h->threads, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t capture_graph(lbm_handle h, int phase, cudaGraphExec_t* exec) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t le = cudaSuccess;
+  for (int t = 0; t < kGraphSteps && le == cudaSuccess; ++t) le = issue_step(h, (phase + t) & 1, h->capture_stream);
+  e = cudaStreamEndCapture(h->capture_stream, &g);
+  if (le != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return le;
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  return e;
+}
+
+int step_impl(lbm_handle h, int32_t n, bool use_graphs) {
+  int32_t done = 0;
+  if (use_graphs) {
+    while (n - done >= kGraphSteps) {
+      cudaGraphExec_t& g = h->graph[h->phase];
+      if (!g) LBM_CUDA(h, capture_graph(h, h->phase, &g), "graph capture");
+      LBM_CUDA(h, cudaGraphLaunch(g, h->stream), "graph launch");
+      done += kGraphSteps;   // even: phase unchanged
+    }
+  }
+  for (; done < n; ++done) {
+    LBM_CUDA(h, issue_step(h, h->phase, h->stream), "sweep launch");
+    h->phase ^= 1;
+  }
+  h->steps += n;
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_last_error(void) { return g_error.c_str(); }
+
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_, void* ctx) {
+  if ((alloc == nullptr) != (free_ == nullptr)) return fail(LBM_ERR_ARG, "alloc and free must both be set or both NULL");
+  std::lock_guard<std::mutex> lock(g_alloc_mu);
+  g_alloc = alloc;
+  g_free = free_;
+  g_alloc_ctx = ctx;
+  return LBM_OK;
+}
+
+int lbm_create_lattice(const lbm_desc* desc, void* cuda_stream, lbm_handle* out) {
+  return create_impl(desc, 1, cuda_stream, out);
+}
+
+int lbm_create_batch(const lbm_desc* descs, int32_t count, void* cuda_stream, lbm_handle* out) {
+  return create_impl(descs, count, cuda_stream, out);
+}
+
+int lbm_destroy(lbm_handle h) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  cudaStreamSynchronize(h->stream);
+  h->drop_graphs();
+  for (Lattice& L : h->lat) {
+    free_storage(h, L);
+    h->dfree(L.flags, (size_t)L.N);
+  }
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  delete h;
+  return LBM_OK;
+}
+
+int lbm_set_geometry(lbm_handle h, int32_t lattice, const uint8_t* flags) {
+  if (int rc = check_lattice(h, lattice)) return rc;
+  if (!flags) return fail(LBM_ERR_ARG, "null flags");
+  Lattice& L = h->lat[lattice];
+  LBM_CUDA(h, cudaMemcpyAsync(L.flags, flags, (size_t)L.N, cudaMemcpyHostToDevice, h->stream), "copy flags");
+  return finish_geometry(h, L);
+}
+
+int lbm_set_geometry_spheres(lbm_handle h, int32_t lattice, const int32_t* cxyzr, int32_t nspheres) {
+  if (int rc = check_lattice(h, lattice)) return rc;
+  if (nspheres < 0 || (nspheres > 0 && !cxyzr)) return fail(LBM_ERR_ARG, "bad sphere list");
+  for (int32_t s = 0; s < nspheres; ++s)
+    if (cxyzr[4 * s + 3] < 0) return fail(LBM_ERR_ARG, "sphere radius must be >= 0");
+  Lattice& L = h->lat[lattice];
+  LBM_CUDA(h, cudaMemsetAsync(L.flags, 0, (size_t)L.N, h->stream), "memset flags");
+  if (nspheres > 0) {
+    Scratch sph(h, (size_t)nspheres * 4 * sizeof(int32_t));
+    if (!sph.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
+    LBM_CUDA(h, cudaMemcpyAsync(sph.p, cxyzr, (size_t)nspheres * 4 * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                h->stream),
+             "copy spheres");
+    LBM_CUDA(h, launch_voxelize_spheres(L.desc.nx, L.desc.ny, L.desc.nz, sph.as<int32_t>(), nspheres,
+                                        kSolidHalfway, L.flags, h->stream),
+             "voxelize");
+  }
+  return finish_geometry(h, L);
+}
+
+int lbm_set_params(lbm_handle h, int32_t lattice, double omega, double Lambda, const double force[3]) {
+  if (int rc = check_handle(h)) return rc;
+  if (lattice < -1 || lattice >= (int32_t)h->lat.size()) return fail(LBM_ERR_ARG, "lattice index out of range");
+  if (!(omega > 0.0 && omega < 2.0)) return fail(LBM_ERR_ARG, "omega must lie in (0, 2)");
+  if (!(Lambda > 0.0) || !std::isfinite(Lambda)) return fail(LBM_ERR_ARG, "Lambda must be positive and finite");
+  const double zero[3] = {0.0, 0.0, 0.0};
+  const double* F = force ? force : zero;
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(F[a])) return fail(LBM_ERR_ARG, "force must be finite");
+  h->drop_graphs();
+  const int32_t lo = lattice < 0 ? 0 : lattice, hi = lattice < 0 ? (int32_t)h->lat.size() : lattice + 1;
+  for (int32_t k = lo; k < hi; ++k) {
+    fill_trt(h->lat[k], omega, Lambda, F);
+    h->lat[k].params = true;
+  }
+  return LBM_OK;
+}
+
+int lbm_init_equilibrium(lbm_handle h, int32_t lattice, const double* rho, const double* u) {
+  if (int rc = check_lattice(h, lattice)) return rc;
+  Lattice& L = h->lat[lattice];
+  if (!L.geometry) return fail(LBM_ERR_STATE, "set the geometry before the initial state");
+  const size_t nb = (size_t)L.N * sizeof(double);
+  Scratch r(h, rho ? nb : 0), v(h, u ? 3 * nb : 0);
+  if ((rho && !r.p) || (u && !v.p)) return fail(LBM_ERR_OOM, "scratch allocation failed");
+  if (rho) LBM_CUDA(h, cudaMemcpyAsync(r.p, rho, nb, cudaMemcpyHostToDevice, h->stream), "copy rho");
+  if (u) LBM_CUDA(h, cudaMemcpyAsync(v.p, u, 3 * nb, cudaMemcpyHostToDevice, h->stream), "copy u");
+  LBM_CUDA(h, launch_from_canonical(L.view(), current_layout(h), state_buffer(h, L), nullptr,
+                                    rho ? r.as<double>() : nullptr, u ? v.as<double>() : nullptr, h->stream),
+           "initial state");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "init sync");
+  L.init = true;
+  h->steps = 0;
+  return LBM_OK;
+}
+
+int lbm_write_pdfs(lbm_handle h, int32_t lattice, const double* in, size_t in_len) {
+  if (int rc = check_lattice(h, lattice)) return rc;
+  Lattice& L = h->lat[lattice];
+  if (!L.geometry) return fail(LBM_ERR_STATE, "set the geometry before writing PDFs");
+  if (!in || in_len < (size_t)Q * L.N) return fail(LBM_ERR_ARG, "input must hold 19*N doubles");
+  const size_t nb = (size_t)Q * L.N * sizeof(double);
+  Scratch c(h, nb);
+  if (!c.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
+  LBM_CUDA(h, cudaMemcpyAsync(c.p, in, nb, cudaMemcpyHostToDevice, h->stream), "copy pdfs");
+  LBM_CUDA(h, launch_from_canonical(L.view(), current_layout(h), state_buffer(h, L), c.as<double>(), nullptr,
+                                    nullptr, h->stream),
+           "write state");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "write sync");
+  L.init = true;
+  h->steps = 0;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_handle h, int32_t n) {
+  if (int rc = check_handle(h)) return rc;
+  if (n < 0) return fail(LBM_ERR_ARG, "n must be >= 0");
+  if (int rc = ready_to_step(h)) return rc;
+  return step_impl(h, n, true);
+}
+
+int lbm_synchronize(lbm_handle h) {
+  if (int rc = check_handle(h)) return rc;
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
+  LBM_CUDA(h, cudaGetLastError(), "asynchronous error");
+  return LBM_OK;
+}
+
+int lbm_steps_done(lbm_handle h, int64_t* steps) {
+  if (int rc = check_handle(h)) return rc;
+  if (!steps) return fail(LBM_ERR_ARG, "null output");
+  *steps = h->steps;
+  return LBM_OK;
+}
+
+static int need_state(lbm_handle h, int32_t lattice) {
+  if (int rc = check_lattice(h, lattice)) return rc;
+  const Lattice& L = h->lat[lattice];
+  if (!L.geometry || !L.init) return fail(LBM_ERR_STATE, "no state yet: set geometry and initial state first");
+  return LBM_OK;
+}
+
+int lbm_read_pdfs(lbm_handle h, int32_t lattice, double* out, size_t out_len) {
+  if (int rc = need_state(h, lattice)) return rc;
+  Lattice& L = h->lat[lattice];
+  if (!out || out_len < (size_t)Q * L.N) return fail(LBM_ERR_ARG, "output must hold 19*N doubles");
+  const size_t nb = (size_t)Q * L.N * sizeof(double);
+  Scratch c(h, nb);
+  if (!c.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
+  LBM_CUDA(h, launch_to_canonical(L.view(), current_layout(h), state_buffer(h, L), c.as<double>(), h->stream),
+           "read state");
+  LBM_CUDA(h, cudaMemcpyAsync(out, c.p, nb, cudaMemcpyDeviceToHost, h->stream), "copy pdfs");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "read sync");
+  return LBM_OK;
+}
+
+int lbm_read_macroscopic(lbm_handle h, int32_t lattice, double* rho, double* u) {
+  if (int rc = need_state(h, lattice)) return rc;
+  Lattice& L = h->lat[lattice];
+  const size_t nb = (size_t)L.N * sizeof(double);
+  Scratch r(h, rho ? nb : 0), v(h, u ? 3 * nb : 0);
+  if ((rho && !r.p) || (u && !v.p)) return fail(LBM_ERR_OOM, "scratch allocation failed");
+  LBM_CUDA(h, launch_macroscopic(L.view(), current_layout(h), state_buffer(h, L), L.trt.force,
+                                 rho ? r.as<double>() : nullptr, u ? v.as<double>() : nullptr, h->stream),
+           "macroscopic");
+  if (rho) LBM_CUDA(h, cudaMemcpyAsync(rho, r.p, nb, cudaMemcpyDeviceToHost, h->stream), "copy rho");
+  if (u) LBM_CUDA(h, cudaMemcpyAsync(u, v.p, 3 * nb, cudaMemcpyDeviceToHost, h->stream), "copy u");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "macroscopic sync");
+  return LBM_OK;
+}
+
+int lbm_read_profile(lbm_handle h, int32_t lattice, int32_t axis, int32_t comp, double* out, size_t out_len) {
+  if (int rc = need_state(h, lattice)) return rc;
+  if (axis < 0 || axis > 2 || comp < 0 || comp > 2) return fail(LBM_ERR_ARG, "axis and comp must be 0..2");
+  Lattice& L = h->lat[lattice];
+  const int planes = axis == 0 ? L.desc.nx : (axis == 1 ? L.desc.ny : L.desc.nz);
+  if (!out || out_len < (size_t)planes) return fail(LBM_ERR_ARG, "output must hold one value per plane");
+  Scratch sc(h, (size_t)planes * (sizeof(double) + sizeof(unsigned long long)));
+  if (!sc.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
+  double* sums = sc.as<double>();
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(sums + planes);
+  LBM_CUDA(h, launch_profile(L.view(), current_layout(h), state_buffer(h, L), L.trt.force, axis, comp, sums, cnt,
+                             h->stream),
+           "profile");
+  std::vector<double> hs(planes);
+  std::vector<unsigned long long> hc(planes);
+  LBM_CUDA(h, cudaMemcpyAsync(hs.data(), sums, planes * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy");
+  LBM_CUDA(h, cudaMemcpyAsync(hc.data(), cnt, planes * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream),
+           "copy");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "profile sync");
+  for (int p = 0; p < planes; ++p) out[p] = hc[p] ? hs[p] / (double)hc[p] : 0.0;
+  return LBM_OK;
+}
+
+int lbm_read_moments(lbm_handle h, int32_t lattice, double out[4]) {
+  if (int rc = need_state(h, lattice)) return rc;
+  if (!out) return fail(LBM_ERR_ARG, "null output");
+  Lattice& L = h->lat[lattice];
+  const LatticeView v = L.view();
+  const int blocks = moments_blocks(v);
+  Scratch sc(h, ((size_t)blocks * 4 + 4) * sizeof(double));
+  if (!sc.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
+  double* partials = sc.as<double>();
+  double* d_out = partials + (size_t)blocks * 4;
+  LBM_CUDA(h, launch_moments(v, current_layout(h), state_buffer(h, L), partials, blocks, d_out, h->stream),
+           "moments");
+  LBM_CUDA(h, cudaMemcpyAsync(out, d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy moments");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "moments sync");
+  return LBM_OK;
+}
+
+int lbm_read_flags(lbm_handle h, int32_t lattice, uint8_t* out, size_t out_len) {
+  if (int rc = check_lattice(h, lattice)) return rc;
+  Lattice& L = h->lat[lattice];
+  if (!L.geometry) return fail(LBM_ERR_STATE, "no geometry set");
+  if (!out || out_len < (size_t)L.N) return fail(LBM_ERR_ARG, "output must hold N bytes");
+  LBM_CUDA(h, cudaMemcpyAsync(out, L.flags, (size_t)L.N, cudaMemcpyDeviceToHost, h->stream), "copy flags");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "flags sync");
+  return LBM_OK;
+}
+
+int lbm_fluid_count(lbm_handle h, int32_t lattice, int64_t* n_fluid) {
+  if (int rc = check_lattice(h, lattice)) return rc;
+  if (!n_fluid) return fail(LBM_ERR_ARG, "null output");
+  if (!h->lat[lattice].geometry) return fail(LBM_ERR_STATE, "no geometry set");
+  *n_fluid = h->lat[lattice].nf;
+  return LBM_OK;
+}
+
+int lbm_read_adjacency(lbm_handle h, int32_t lattice, int32_t* out, size_t out_len) {
+  if (int rc = check_lattice(h, lattice)) return rc;
+  Lattice& L = h->lat[lattice];
+  if (!L.geometry) return fail(LBM_ERR_STATE, "no geometry set");
+  if (!L.indirect()) return fail(LBM_ERR_ARG, "the lattice uses direct addressing: it has no adjacency list");
+  if (!out || out_len < (size_t)18 * L.nf) return fail(LBM_ERR_ARG, "output must hold 18*Nf int32");
+  if (L.nf > 0)
+    LBM_CUDA(h, cudaMemcpy2DAsync(out, (size_t)L.nf * sizeof(int32_t), L.adj, (size_t)L.stride * sizeof(int32_t),
+                                  (size_t)L.nf * sizeof(int32_t), 18, cudaMemcpyDeviceToHost, h->stream),
+             "copy adjacency");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "adjacency sync");
+  return LBM_OK;
+}
+
+int lbm_set_tuning(lbm_handle h, int32_t threads, int32_t cells_per_thread, int32_t tile_cells) {
+  if (int rc = check_handle(h)) return rc;
+  if (threads != 0 && (threads < 32 || threads > 512 || threads % 32 != 0))
+    return fail(LBM_ERR_ARG, "threads must be a multiple of 32 in [32, 512]");
+  if (cells_per_thread != 0 && cells_per_thread != 1) return fail(LBM_ERR_UNSUPPORTED, "cells_per_thread must be 1");
+  if (tile_cells < 0) return fail(LBM_ERR_ARG, "tile_cells must be >= 0");
+  h->drop_graphs();
+  if (threads) h->threads = threads;
+  if (cells_per_thread) h->cells_per_thread = cells_per_thread;
+  if (tile_cells) h->tile_cells = tile_cells;
+  return LBM_OK;
+}
+
+int lbm_get_tuning(lbm_handle h, int32_t out[3]) {
+  if (int rc = check_handle(h)) return rc;
+  if (!out) return fail(LBM_ERR_ARG, "null output");
+  out[0] = h->threads;
+  out[1] = h->cells_per_thread;
+  out[2] = h->tile_cells;
+  return LBM_OK;
+}
+
+int lbm_autotune(lbm_handle h, int32_t steps) {
+  if (int rc = check_handle(h)) return rc;
+  if (steps < 2) return fail(LBM_ERR_ARG, "steps must be >= 2");
+  if (int rc = ready_to_step(h)) return rc;
+  steps += steps & 1;   // even: the AA parity and the pull buffers come back
+  // save every lattice's state so the trials leave no trace
+  std::vector<void*> saved(h->lat.size(), nullptr);
+  const int phase0 = h->phase;
+  const int64_t steps0 = h->steps;
+  for (size_t k = 0; k < h->lat.size(); ++k) {
+    Lattice& L = h->lat[k];
+    saved[k] = h->dalloc(pdf_bytes(L, h->prec));
+    if (!saved[k]) {
+      for (size_t j = 0; j < k; ++j) h->dfree(saved[j], pdf_bytes(h->lat[j], h->prec));
+      return fail(LBM_ERR_OOM, "autotune needs a copy of the state");
+    }
+    LBM_CUDA(h, cudaMemcpyAsync(saved[k], state_buffer(h, L), pdf_bytes(L, h->prec), cudaMemcpyDeviceToDevice,
+                                h->stream),
+             "save state");
+  }
+  const int candidates[] = {64, 128, 192, 256, 384, 512};
+  int best = h->threads;
+  float best_ms = 1e30f;
+  for (int t : candidates) {
+    h->threads = t;
+    h->drop_graphs();
+    int rc = step_impl(h, 2, false);   // warm-up
+    if (rc == LBM_OK) {
+      cudaEventRecord(h->ev0, h->stream);
+      rc = step_impl(h, steps, false);
+      cudaEventRecord(h->ev1, h->stream);
+    }
+    if (rc != LBM_OK) break;
+    cudaError_t e = cudaEventSynchronize(h->ev1);
+    if (e != cudaSuccess) return cuda_fail(h, e, "autotune timing");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+  }
+  h->threads = best;
+  h->drop_graphs();
+  h->phase = phase0;
+  h->steps = steps0;
+  for (size_t k = 0; k < h->lat.size(); ++k) {
+    Lattice& L = h->lat[k];
+    LBM_CUDA(h, cudaMemcpyAsync(state_buffer(h, L), saved[k], pdf_bytes(L, h->prec), cudaMemcpyDeviceToDevice,
+                                h->stream),
+             "restore state");
+  }
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "autotune sync");
+  for (size_t k = 0; k < h->lat.size(); ++k) h->dfree(saved[k], pdf_bytes(h->lat[k], h->prec));
+  return h->poisoned ? fail(LBM_ERR_CUDA, "autotune hit a CUDA error") : LBM_OK;
+}
+
+int lbm_memory_bytes(lbm_handle h, int64_t* bytes) {
+  if (int rc = check_handle(h)) return rc;
+  if (!bytes) return fail(LBM_ERR_ARG, "null output");
+  *bytes = h->bytes;
+  return LBM_OK;
+}
+
+int lbm_bench_copy19(const void* src, void* dst, int64_t n, int64_t stride_elems, int32_t elem_bytes,
+                     void* cuda_stream) {
+  if (!src || !dst || n < 0 || stride_elems < n) return fail(LBM_ERR_ARG, "bad copy-19 arguments");
+  cudaError_t e = launch_copy19(src, dst, n, stride_elems, elem_bytes, static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("copy-19: ") + cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int lbm_bench_update19(void* buf, int64_t n, int64_t stride_elems, int32_t elem_bytes, void* cuda_stream) {
+  if (!buf || n < 0 || stride_elems < n) return fail(LBM_ERR_ARG, "bad update-19 arguments");
+  cudaError_t e = launch_update19(buf, n, stride_elems, elem_bytes, static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("update-19: ") + cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// Internal interfaces between the translation units of liblbm_gb300.so:
+// the launchers each .cu file provides and the handle the C ABI manages.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "lbm_gb300.h"
+
+namespace lbm {
+
+// Where the state of a lattice sits in its storage after t steps.
+//   kCanonical: slot i of node x holds f_i(x, t).
+//   kPullForm : slot i of node x holds f*_i(x, t-1), the post-collision value
+//               that streams to x + c_i; so f_i(x, t) sits in slot i of x - c_i
+//               (in slot opp(i) of x across a half-way link). Two-grid pull.
+//   kAAForm   : as kPullForm, but in slot opp(i) (in slot i of x across a
+//               half-way link). The AA pattern after an odd number of steps.
+enum Layout : int { kCanonical = 0, kPullForm = 1, kAAForm = 2 };
+
+enum Prec : int { kF64 = 0, kF32 = 1, kF16 = 2 };
+
+enum SweepKind : int { kPull = 0, kAAEven = 1, kAAOdd = 2 };
+
+inline int elem_bytes(int prec) { return prec == kF64 ? 8 : (prec == kF32 ? 4 : 2); }
+
+// Everything a kernel needs to address one lattice's storage.
+struct LatticeView {
+  int nx = 0, ny = 0, nz = 0;
+  int64_t n_cells = 0;    // N
+  int64_t n_nodes = 0;    // N (direct) or Nf (indirect)
+  int64_t stride = 0;     // elements between direction arrays, multiple of 128
+  int prec = kF64;
+  bool indirect = false;
+  bool has_halfway = false;
+  const uint8_t* flags = nullptr;     // [N]
+  const int32_t* adj = nullptr;       // [18][stride], indirect only
+  const int32_t* cell_of = nullptr;   // [Nf], indirect only
+  const int32_t* list_index = nullptr;  // [N] node of each cell or -1, indirect only
+};
+
+struct TrtParams {
+  double omega_p = 1.0, omega_m = 1.0;
+  double fk[9] = {0};     // 3 w_k (c_k . F), k = 1..9
+  double force[3] = {0};
+};
+
+// ------------------------------------------------------------ sweep launchers
+// One time step of one lattice. src == dst for the AA kinds.
+cudaError_t launch_sweep(const LatticeView& v, SweepKind kind, const void* src, void* dst,
+                         const TrtParams& p, int threads, cudaStream_t s);
+
+
+// ------------------------------------------------------- state conversions
+// Write storage `dst` in `layout` from canonical FP64 values, which come either
+// from a device array canon[19][N] (non-null) or, if canon is null, from the
+// equilibrium of rho[N] / u[3][N] (either may be null: 1 / 0).
+cudaError_t launch_from_canonical(const LatticeView& v, Layout layout, void* dst, const double* canon,
+                                  const double* rho, const double* u, cudaStream_t s);
+// Canonical FP64 out[19][N] from storage in `layout` (0 at half-way solid cells).
+cudaError_t launch_to_canonical(const LatticeView& v, Layout layout, const void* src, double* out,
+                                cudaStream_t s);
+// rho[N], u[3][N] (either may be null) from storage in `layout`.
+cudaError_t launch_macroscopic(const LatticeView& v, Layout layout, const void* src, const double force[3],
+                               double* rho, double* u, cudaStream_t s);
+// Per-plane sums over fluid cells of u_comp (out[n_axis]) and fluid counts
+// (cnt[n_axis]); the caller divides.
+cudaError_t launch_profile(const LatticeView& v, Layout layout, const void* src, const double force[3],
+                           int axis, int comp, double* sums, unsigned long long* counts, cudaStream_t s);
+// FP64 mass and momentum over all stored PDFs: per-block partials written to
+// `partials` (4 doubles per block, `blocks` blocks), then reduced in a fixed
+// order into out[4].
+int moments_blocks(const LatticeView& v);
+cudaError_t launch_moments(const LatticeView& v, Layout layout, const void* src, double* partials, int blocks,
+                           double* out, cudaStream_t s);
+
+// ------------------------------------------------------------- geometry
+cudaError_t launch_voxelize_spheres(int nx, int ny, int nz, const int32_t* d_spheres, int nspheres,
+                                    uint8_t value, uint8_t* d_flags, cudaStream_t s);
+// Fluid compaction: list_index[N] (-1 for solid), cell_of[Nf]; block sums in
+// `scan_tmp` (scan_tmp_elems(N) int32). Returns Nf through *d_nf (device).
+int64_t scan_tmp_elems(int64_t n);
+cudaError_t launch_compact(const uint8_t* d_flags, int64_t n, int32_t* d_list_index, int32_t* d_cell_of,
+                           int32_t* scan_tmp, int64_t* d_nf, cudaStream_t s);
+cudaError_t launch_adjacency(const LatticeView& v, const int32_t* d_list_index, int32_t* d_adj, cudaStream_t s);
+// Fluid cells on the boundary faces, accumulated into out[6] (zeroed by the
+// caller): out[2a] on the low face of axis a, out[2a+1] on the high face.
+cudaError_t launch_face_fluid(const uint8_t* d_flags, int nx, int ny, int nz, unsigned long long* d_out,
+                              cudaStream_t s);
+// Count flags into out[4] (zeroed by the caller): cells with flag 0, 1, 2, other.
+cudaError_t launch_count_flags(const uint8_t* d_flags, int64_t n, unsigned long long* d_out, cudaStream_t s);
+
+// ---------------------------------------------------------- micro-benchmarks
+cudaError_t launch_copy19(const void* src, void* dst, int64_t n, int64_t stride, int elem, cudaStream_t s);
+cudaError_t launch_update19(void* buf, int64_t n, int64_t stride, int elem, cudaStream_t s);
+
+}  // namespace lbm

@@ -1,0 +1,164 @@
+// D3Q19 TRT model on the device: direction table, storage formats and the
+// fused collision (Sec. 2 of Wittmann et al., arXiv 1711.11468: D3Q19, TRT,
+// constant body force for verification).
+//
+// Direction order is the ABI's: 0 rest; k = 1..9 the "positive" directions
+// (1,0,0) (0,1,0) (0,0,1) (1,1,0) (1,-1,0) (1,0,1) (1,0,-1) (0,1,1) (0,1,-1);
+// k + 9 the opposite of k. The collision works on the nine opposite pairs,
+// which is how TRT is defined (symmetric / antisymmetric parts per pair).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cstdint>
+
+namespace lbm {
+
+constexpr int Q = 19;
+
+// Velocity components by direction, written out per axis.
+__host__ __device__ constexpr int cx(int i) {
+  return (i == 1 || i == 4 || i == 5 || i == 6 || i == 7) ? 1
+       : (i == 10 || i == 13 || i == 14 || i == 15 || i == 16) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy(int i) {
+  return (i == 2 || i == 4 || i == 8 || i == 9 || i == 14) ? 1
+       : (i == 5 || i == 11 || i == 13 || i == 17 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz(int i) {
+  return (i == 3 || i == 6 || i == 8 || i == 16 || i == 18) ? 1
+       : (i == 7 || i == 9 || i == 12 || i == 15 || i == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i <= 9 ? i + 9 : i - 9); }
+// 1/3 at rest, 1/18 on the faces (k = 1..3 and their opposites), 1/36 on the edges.
+__host__ __device__ constexpr double weight(int i) {
+  return i == 0 ? 1.0 / 3.0 : (((i - 1) % 9) < 3 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// Compile-time checks of the table against the listed vectors and the pairing.
+constexpr bool table_ok() {
+  constexpr int v[10][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0},
+                            {1, -1, 0}, {1, 0, 1}, {1, 0, -1}, {0, 1, 1}, {0, 1, -1}};
+  for (int k = 0; k <= 9; ++k) {
+    if (cx(k) != v[k][0] || cy(k) != v[k][1] || cz(k) != v[k][2]) return false;
+    if (k > 0 && (cx(k + 9) != -v[k][0] || cy(k + 9) != -v[k][1] || cz(k + 9) != -v[k][2])) return false;
+    if (k > 0 && (opp(opp(k)) != k || opp(k) != k + 9)) return false;
+    const int c2 = v[k][0] * v[k][0] + v[k][1] * v[k][1] + v[k][2] * v[k][2];
+    if (k > 0 && weight(k) != (c2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0)) return false;
+  }
+  return true;
+}
+static_assert(table_ok(), "D3Q19 direction table does not match the ABI order");
+
+enum Flag : uint8_t { kFluid = 0, kSolidFullway = 1, kSolidHalfway = 2 };
+
+// TRT parameters in the arithmetic type A. fk[k-1] = 3 w_k (c_k . F) is the
+// body-force source of direction k (its opposite gets -fk).
+template <typename A>
+struct Trt {
+  A omega_p, omega_m;
+  A fk[9];
+};
+
+// ---------------------------------------------------------------- storage
+// FP64 stores f_i; FP32 and FP16 store the deviation d_i = f_i - w_i from the
+// rest state, collided in FP32. The shift keeps the stored magnitudes near the
+// small departures that carry the flow, instead of near w_i.
+template <typename S>
+struct Storage;
+
+template <>
+struct Storage<double> {
+  using A = double;
+  static constexpr bool kShifted = false;
+  __device__ __forceinline__ static double load(const double* p) { return __ldcs(p); }
+  __device__ __forceinline__ static void store(double* p, double v) { __stcs(p, v); }
+  __device__ __forceinline__ static double to_f64(double v, int) { return v; }
+  __device__ __forceinline__ static double from_f64(double f, int) { return f; }
+};
+
+template <>
+struct Storage<float> {
+  using A = float;
+  static constexpr bool kShifted = true;
+  __device__ __forceinline__ static float load(const float* p) { return __ldcs(p); }
+  __device__ __forceinline__ static void store(float* p, float v) { __stcs(p, v); }
+  __device__ __forceinline__ static double to_f64(float v, int i) { return weight(i) + (double)v; }
+  __device__ __forceinline__ static float from_f64(double f, int i) { return __double2float_rn(f - weight(i)); }
+};
+
+template <>
+struct Storage<__half> {
+  using A = float;
+  static constexpr bool kShifted = true;
+  __device__ __forceinline__ static float load(const __half* p) {
+    return __half2float(__ushort_as_half(__ldcs(reinterpret_cast<const unsigned short*>(p))));
+  }
+  __device__ __forceinline__ static void store(__half* p, float v) {
+    __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(__float2half_rn(v)));
+  }
+  __device__ __forceinline__ static double to_f64(__half v, int i) { return weight(i) + (double)__half2float(v); }
+  __device__ __forceinline__ static __half from_f64(double f, int i) {
+    // FP64 -> FP16 in one rounding (a detour through FP32 could double-round).
+    return __double2half(f - weight(i));
+  }
+};
+
+// ---------------------------------------------------------------- collision
+// TRT collision plus body force on one node, in place on f[19].
+//   rho = sum f_i, j = sum c_i f_i, u = j / rho,
+//   e_i = w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u),
+//   per pair (k, k+9): f+ = (f_k + f_k+9)/2, f- = (f_k - f_k+9)/2 (same for e),
+//   f*_k = f_k - w+ (f+ - e+) - w- (f- - e-) + 3 w_k c_k.F, f*_k+9 mirrored.
+// With kShifted, f holds d_i = f_i - w_i: then rho = 1 + sum d_i, j = sum c_i d_i
+// (sum c_i w_i = 0), and e_i - w_i = w_i (drho - 3/2 rho u.u + 3 c.j + 9/2 (c.u)(c.j)),
+// which is the same pairwise algebra with rho replaced by drho in the constant term.
+template <typename A, bool kShifted>
+__device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
+  A s[10], d[10];
+#pragma unroll
+  for (int k = 1; k <= 9; ++k) {
+    s[k] = f[k] + f[k + 9];
+    d[k] = f[k] - f[k + 9];
+  }
+  const A rho0 = f[0] + (((s[1] + s[2]) + (s[3] + s[4])) + ((s[5] + s[6]) + (s[7] + s[8])) + s[9]);
+  const A rho = kShifted ? A(1) + rho0 : rho0;
+  const A jx = (d[1] + d[4]) + (d[5] + d[6]) + d[7];
+  const A jy = (d[2] + d[4]) - d[5] + (d[8] + d[9]);
+  const A jz = (d[3] + d[6]) - d[7] + (d[8] - d[9]);
+  const A inv_rho = A(1) / rho;
+  const A ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+  const A usq = ux * ux + uy * uy + uz * uz;
+  // constant part of e+ per weight: w (rho0 - 3/2 rho u.u)
+  const A base = rho0 - A(1.5) * rho * usq;
+  constexpr A w0 = A(1.0 / 3.0), wf = A(1.0 / 18.0), we = A(1.0 / 36.0);
+  const A base_f = wf * base, base_e = we * base;
+  const A half = A(0.5);
+
+  // rest direction: only the symmetric part relaxes
+  f[0] = f[0] - p.omega_p * (f[0] - w0 * base);
+
+#pragma unroll
+  for (int k = 1; k <= 9; ++k) {
+    const A cu = A(cx(k)) * ux + A(cy(k)) * uy + A(cz(k)) * uz;
+    const A cj = A(cx(k)) * jx + A(cy(k)) * jy + A(cz(k)) * jz;
+    const A w = (k <= 3) ? wf : we;
+    const A eplus = ((k <= 3) ? base_f : base_e) + (A(4.5) * w) * (cu * cj);
+    const A eminus = (A(3) * w) * cj;
+    const A dplus = p.omega_p * (half * s[k] - eplus);
+    const A dminus = p.omega_m * (half * d[k] - eminus) - p.fk[k - 1];
+    f[k] = f[k] - dplus - dminus;
+    f[k + 9] = f[k + 9] - dplus + dminus;
+  }
+}
+
+// Equilibrium in FP64, absolute or shifted by w_i (initialisation only).
+__device__ __forceinline__ double equilibrium_f64(int i, double rho, double ux, double uy, double uz,
+                                                  bool shifted) {
+  const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+  const double usq = ux * ux + uy * uy + uz * uz;
+  const double w = weight(i);
+  if (!shifted) return w * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+  return w * ((rho - 1.0) + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
+}
+
+}  // namespace lbm

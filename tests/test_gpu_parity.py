@@ -1,0 +1,250 @@
+"""GPU parity: the CUDA sweep through the C ABI against the FP64 oracle.
+
+FP64 storage must match the oracle to max |df| <= 1e-12 (the FMA-contracted
+device arithmetic differs from the oracle's plain rounding by a few ulp per
+step; 1e-12 leaves three orders of magnitude over what 100 steps accumulate).
+Index and geometry work is compared bit for bit.
+"""
+import numpy as np
+import pytest
+
+from paper_1711_11468_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+LAM = 3.0 / 16.0
+TOL_F64 = 1e-12
+
+
+def gpu_run(lbm, dims, *, flags=None, spheres=None, prec=0, addr=0, prop=1, omega=1.0, Lam=LAM, F=(0, 0, 0),
+            rho=None, u=None, f0=None, steps=0, threads=0, periodic=(1, 1, 1), read="pdfs"):
+    import torch
+    desc = lbm.make_desc(dims, prec, addr, prop, periodic)
+    h = lbm.lbm_create_lattice(desc, torch.cuda.current_stream())
+    try:
+        if threads:
+            lbm.lbm_set_tuning(h, threads, 0, 0)
+        if spheres is not None:
+            lbm.lbm_set_geometry_spheres(h, 0, spheres)
+        else:
+            lbm.lbm_set_geometry(h, 0, flags)
+        lbm.lbm_set_params(h, 0, omega, Lam, F)
+        if f0 is not None:
+            lbm.lbm_write_pdfs(h, 0, f0)
+        else:
+            lbm.lbm_init_equilibrium(h, 0, rho, u)
+        lbm.lbm_step(h, steps)
+        out = {}
+        if "pdfs" in read:
+            out["pdfs"] = lbm.lbm_read_pdfs(h, 0)
+        if "flags" in read:
+            out["flags"] = lbm.lbm_read_flags(h, 0)
+        if "adj" in read:
+            out["adj"] = lbm.lbm_read_adjacency(h, 0)
+        if "moments" in read:
+            out["moments"] = lbm.lbm_read_moments(h, 0)
+        if "macro" in read:
+            out["macro"] = lbm.lbm_read_macroscopic(h, 0)
+        if "profile" in read:
+            out["profile"] = lbm.lbm_read_profile(h, 0, 1, 0)
+        return out
+    finally:
+        lbm.lbm_destroy(h)
+
+
+def random_flags(rng, dims, indirect):
+    fl = np.zeros(int(np.prod(dims)), dtype=np.uint8)
+    r = rng.random(fl.size)
+    if indirect:
+        fl[r < 0.25] = 2
+    else:
+        fl[r < 0.12] = 1
+        fl[(r >= 0.12) & (r < 0.25)] = 2
+    return fl
+
+
+def random_state(orc, rng, dims, flags):
+    N = int(np.prod(dims))
+    rho = 1.0 + 0.05 * (rng.random(N) - 0.5)
+    u = 0.05 * (rng.random((3, N)) - 0.5)
+    f = orc.init_equilibrium(dims, flags, rho, u)
+    noise = 1e-3 * (rng.random(f.shape) - 0.5)
+    noise[:, flags == 2] = 0.0
+    return f + noise
+
+
+# ---------------------------------------------------- Poiseuille, 64^3, FP64
+@pytest.mark.parametrize("prop", [0, 1])
+@pytest.mark.parametrize("steps", [100, 99])
+def test_poiseuille_64_f64(lbm, orc, prop, steps):
+    """The paper's verification set-up (Sec. 2.1) on 64^3: walls at y = 0, 63."""
+    c = inputs.POISEUILLE_64
+    dims = c["dims"]
+    fl = inputs.channel_flags(*dims)
+    out = gpu_run(lbm, dims, flags=fl, prop=prop, omega=c["omega"], F=c["force"], steps=steps,
+                  periodic=(1, 0, 1), read="pdfs,moments,profile")
+    f0 = orc.init_equilibrium(dims, fl)
+    ref = orc.run(dims, fl, c["omega"], orc.omega_minus(c["omega"], c["Lambda"]), c["force"], f0, steps)
+    assert np.abs(out["pdfs"] - ref).max() <= TOL_F64
+    m0 = f0.sum()
+    assert abs(out["moments"][0] - m0) / m0 <= 1e-13
+    _, u = orc.macroscopic(dims, fl, c["force"], ref)
+    prof_ref = u[0].reshape(dims[2], dims[1], dims[0]).mean(axis=(0, 2))
+    assert np.abs(out["profile"][1:-1] - prof_ref[1:-1]).max() <= 1e-12 * np.abs(prof_ref).max() + 1e-18
+
+
+# ------------------------------------------- random small lattices, FP64
+CASES = [((37, 11, 9), 32), ((5, 4, 3), 256), ((40, 6, 7), 64), ((2, 3, 2), 32)]
+
+
+@pytest.mark.parametrize("dims,threads", CASES)
+@pytest.mark.parametrize("addr", [0, 1])
+@pytest.mark.parametrize("prop", [0, 1])
+def test_random_lattices_f64(lbm, orc, dims, threads, addr, prop):
+    rng = np.random.default_rng(abs(hash((dims, addr, prop))) % 2 ** 32)
+    fl = random_flags(rng, dims, addr == 1)
+    f0 = random_state(orc, rng, dims, fl)
+    omega = rng.uniform(0.6, 1.8)
+    Lam = rng.uniform(0.05, 0.5)
+    F = 1e-4 * (rng.random(3) - 0.5)
+    wm = orc.omega_minus(omega, Lam)
+    ref = f0
+    done = 0
+    for steps in (1, 2, 5):
+        out = gpu_run(lbm, dims, flags=fl, addr=addr, prop=prop, omega=omega, Lam=Lam, F=F, f0=f0, steps=steps,
+                      threads=threads)
+        ref = orc.run(dims, fl, omega, wm, F, ref, steps - done)
+        done = steps
+        assert np.abs(out["pdfs"] - ref).max() <= 1e-13, (steps, np.abs(out["pdfs"] - ref).max())
+
+
+# --------------------------------------------------- geometry, bit-exact
+@pytest.mark.parametrize("dims", [(48, 40, 36), (33, 17, 65)])
+def test_sphere_geometry_and_adjacency_bitexact(lbm, orc, dims):
+    pack = inputs.sphere_pack(dims, 7, 2, 9, 0.6, nonoverlap_attempts=5000, mc_points=20000)
+    out = gpu_run(lbm, dims, spheres=pack.spheres, addr=1, read="flags,adj")
+    fl = orc.voxelize_spheres(dims, pack.spheres, 2)
+    assert np.array_equal(out["flags"], fl)
+    _, _, adj = orc.build_list(dims, fl)
+    assert out["adj"].shape == adj.shape
+    assert np.array_equal(out["adj"], adj)
+
+
+def test_spheres_large_radius_wraps(lbm, orc):
+    dims = (10, 12, 9)
+    sph = np.array([[0, 0, 0, 6], [9, 11, 8, 2], [5, 5, 5, 0]], dtype=np.int32)
+    out = gpu_run(lbm, dims, spheres=sph, addr=1, read="flags,adj")
+    fl = orc.voxelize_spheres(dims, sph, 2)
+    assert np.array_equal(out["flags"], fl)
+    assert np.array_equal(out["adj"], orc.build_list(dims, fl)[2])
+
+
+# ------------------------------------------------------- state handling
+@pytest.mark.parametrize("addr", [0, 1])
+@pytest.mark.parametrize("prop", [0, 1])
+def test_write_read_roundtrip_bitexact(lbm, orc, addr, prop):
+    rng = np.random.default_rng(11)
+    dims = (13, 9, 7)
+    fl = random_flags(rng, dims, addr == 1)
+    f0 = random_state(orc, rng, dims, fl)
+    out = gpu_run(lbm, dims, flags=fl, addr=addr, prop=prop, f0=f0, steps=0)
+    assert np.array_equal(out["pdfs"], f0)
+
+
+@pytest.mark.parametrize("addr", [0, 1])
+@pytest.mark.parametrize("prop", [0, 1])
+def test_checkpoint_resume_bitexact(lbm, orc, addr, prop):
+    import torch
+    rng = np.random.default_rng(12)
+    dims = (16, 10, 6)
+    fl = random_flags(rng, dims, addr == 1)
+    f0 = random_state(orc, rng, dims, fl)
+    kw = dict(flags=fl, addr=addr, prop=prop, omega=1.3, F=(1e-5, 0, 0))
+    full = gpu_run(lbm, dims, f0=f0, steps=14, **kw)["pdfs"]
+    half = gpu_run(lbm, dims, f0=f0, steps=7, **kw)["pdfs"]
+    resumed = gpu_run(lbm, dims, f0=half, steps=7, **kw)["pdfs"]
+    assert np.array_equal(full, resumed)
+    torch.cuda.synchronize()
+
+
+def test_aa_equals_pull_bitwise(lbm, orc):
+    rng = np.random.default_rng(13)
+    dims = (30, 14, 12)
+    fl = random_flags(rng, dims, False)
+    f0 = random_state(orc, rng, dims, fl)
+    for steps in (2, 6, 17):
+        a = gpu_run(lbm, dims, flags=fl, prop=0, omega=0.9, F=(1e-5, 1e-6, 0), f0=f0, steps=steps)["pdfs"]
+        b = gpu_run(lbm, dims, flags=fl, prop=1, omega=0.9, F=(1e-5, 1e-6, 0), f0=f0, steps=steps)["pdfs"]
+        assert np.array_equal(a, b)
+
+
+def test_list_equals_dense_on_periodic_box(lbm, orc):
+    rng = np.random.default_rng(14)
+    dims = (20, 12, 10)
+    fl = np.zeros(int(np.prod(dims)), dtype=np.uint8)
+    f0 = random_state(orc, rng, dims, fl)
+    for prop in (0, 1):
+        a = gpu_run(lbm, dims, flags=fl, addr=0, prop=prop, omega=1.7, F=(0, 1e-5, 0), f0=f0, steps=9)["pdfs"]
+        b = gpu_run(lbm, dims, flags=fl, addr=1, prop=prop, omega=1.7, F=(0, 1e-5, 0), f0=f0, steps=9)["pdfs"]
+        assert np.array_equal(a, b)
+
+
+# ------------------------------------------------- reduced-precision storage
+@pytest.mark.parametrize("prec,tol", [(1, 5e-6), (2, 0.1)])
+def test_shifted_storage_poiseuille_error(lbm, orc, prec, tol):
+    """FP32 / FP16 storage of f - w with FP32 arithmetic on the 64^3 channel:
+    the mean velocity profile against the FP64 oracle (max-relative)."""
+    c = inputs.POISEUILLE_64
+    dims = c["dims"]
+    fl = inputs.channel_flags(*dims)
+    out = gpu_run(lbm, dims, flags=fl, prec=prec, omega=c["omega"], F=c["force"], steps=100, periodic=(1, 0, 1),
+                  read="profile")
+    ref = orc.run(dims, fl, c["omega"], orc.omega_minus(c["omega"], c["Lambda"]), c["force"],
+                  orc.init_equilibrium(dims, fl), 100)
+    _, u = orc.macroscopic(dims, fl, c["force"], ref)
+    prof = u[0].reshape(dims[2], dims[1], dims[0]).mean(axis=(0, 2))
+    err = np.abs(out["profile"] - prof).max() / np.abs(prof).max()
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_shifted_rest_state_exact(lbm, orc, prec):
+    """Shifted storage keeps the rest state exactly at zero deviation."""
+    dims = (16, 8, 8)
+    fl = inputs.channel_flags(*dims)
+    out = gpu_run(lbm, dims, flags=fl, prec=prec, omega=1.4, steps=20, periodic=(1, 0, 1))
+    w = orc.weights()
+    live = fl != 2
+    assert np.array_equal(out["pdfs"][:, live], np.repeat(w[:, None], live.sum(), 1))
+
+
+# ------------------------------------------------------------ error paths
+def test_error_paths(lbm):
+    import torch
+    s = torch.cuda.current_stream()
+    dims = (8, 8, 8)
+    h = lbm.lbm_create_lattice(lbm.make_desc(dims, 0, 1, 1), s)
+    try:
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_step(h, 1)
+        assert e.value.code == lbm.LBM_ERR_STATE
+        fl = inputs.channel_flags(*dims)
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_set_geometry(h, 0, fl)     # flag 1 with indirect addressing
+        assert e.value.code == lbm.LBM_ERR_ARG
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_set_params(h, 0, 2.0, LAM)
+        assert e.value.code == lbm.LBM_ERR_ARG
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_read_pdfs(h, 0)
+        assert e.value.code == lbm.LBM_ERR_STATE
+    finally:
+        lbm.lbm_destroy(h)
+    h = lbm.lbm_create_lattice(lbm.make_desc(dims, 0, 0, 1, periodic=(1, 0, 0)), s)
+    try:
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_set_geometry(h, 0, inputs.channel_flags(*dims))   # z open but not walled
+        assert e.value.code == lbm.LBM_ERR_ARG
+        lbm.lbm_set_geometry(h, 0, inputs.duct_flags(*dims))
+    finally:
+        lbm.lbm_destroy(h)
