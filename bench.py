@@ -189,10 +189,31 @@ def variant(lbm, stream, precision, propagation, steps, nf, peak):
             "roofline_frac": round(gbs / peak, 4), "steps": steps}
 
 
+def run_sweep_only(args):
+    """Profiling mode: build the lattice, then warm-up and timed steps only."""
+    import torch
+
+    from paper_1711_11468_gb300 import lbm
+    torch.cuda.set_device(0)
+    lbm.load()
+    stream = torch.cuda.current_stream()
+    prec = lbm.PRECISION[args.precision]
+    prop = lbm.LBM_AA_INPLACE if args.prop == "aa" else lbm.LBM_PULL_TWO_GRID
+    h, flags = make_duct(lbm, stream, prec, prop)
+    lbm.lbm_step(h, args.warmup)
+    sec = time_steps(lbm, h, args.steps, stream)
+    nf = int(np.count_nonzero(flags == 0))
+    lbm.lbm_destroy(h)
+    print(json.dumps({"mode": "sweep-only", "dims": list(DIMS), "precision": args.precision, "prop": args.prop,
+                      "steps": args.steps, "mflups": round(nf * args.steps / sec / 1e6, 1)}), flush=True)
+
+
 def run_gpu(args):
     import torch
 
     from paper_1711_11468_gb300 import lbm
+    if args.sweep_only:
+        return run_sweep_only(args)
     world, rank, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
     lbm.load()
@@ -326,7 +347,14 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-only", action="store_true", help="profiling: warm-up and timed steps only")
+    ap.add_argument("--dims", type=int, default=0, help="profiling: cubic duct of this size instead of 256")
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32", "f16"], help="profiling (with --sweep-only)")
+    ap.add_argument("--prop", default="aa", choices=["aa", "pull"], help="profiling (with --sweep-only)")
     args = ap.parse_args()
+    if args.dims:
+        global DIMS
+        DIMS = (args.dims, args.dims, args.dims)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

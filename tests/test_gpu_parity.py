@@ -90,7 +90,9 @@ def test_poiseuille_64_f64(lbm, orc, prop, steps):
     assert abs(out["moments"][0] - m0) / m0 <= 1e-13
     _, u = orc.macroscopic(dims, fl, c["force"], ref)
     prof_ref = u[0].reshape(dims[2], dims[1], dims[0]).mean(axis=(0, 2))
-    assert np.abs(out["profile"][1:-1] - prof_ref[1:-1]).max() <= 1e-12 * np.abs(prof_ref).max() + 1e-18
+    # u = (j + F/2)/rho with j a cancelling sum of 19 PDFs of size ~0.1: the
+    # velocity inherits an absolute error of a few tens of ulp(0.1) from the PDFs
+    assert np.abs(out["profile"][1:-1] - prof_ref[1:-1]).max() <= 1e-14
 
 
 # ------------------------------------------- random small lattices, FP64
