@@ -173,6 +173,22 @@ int lbm_read_profile(lbm_handle h, int32_t lattice, int32_t axis, int32_t comp, 
  * (momentum). Synchronous. */
 int lbm_read_moments(lbm_handle h, int32_t lattice, double out[4]);
 
+/* The same sums as lbm_read_moments, computed by the same kernels, but this
+ * call allocates no device memory: it neither calls cudaMalloc/cudaFree nor
+ * goes through the allocator hook. It is meant for callers that must not
+ * allocate while they run, for example code whose memory budget is fixed up
+ * front, or a host whose allocator is busy in a section it cannot re-enter.
+ * The paper has no counterpart: this is a deployment convenience.
+ *
+ * The scratch is one static device array of 32,772 doubles (256 KiB) that every
+ * GPU which loads the library keeps until the process exits. Lattices with more
+ * than 134,217,728 cells are rejected with LBM_ERR_ARG. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before capturing any stream into a CUDA graph. All calls share the
+ * array: calls whose work overlaps on a GPU (other threads, other streams) race
+ * and must be serialised by the caller. Synchronous on the handle's stream. */
+int lbm_read_moments_noalloc(lbm_handle h, int32_t lattice, double out[4]);
+
 /* Flags uint8[N] of one lattice as the library holds them (for spheres: the
  * device voxelisation). Synchronous. */
 int lbm_read_flags(lbm_handle h, int32_t lattice, uint8_t* out, size_t out_len);

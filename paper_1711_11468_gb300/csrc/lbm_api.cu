@@ -704,3 +704,62 @@ int lbm_bench_update19(void* buf, int64_t n, int64_t stride_elems, int32_t elem_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// lbm_read_moments_noalloc: the moments reduction with its scratch in a static
+// device array instead of memory from the allocator, for callers that may not
+// allocate (see the header).
+namespace {
+
+constexpr int kStaticMomentBlocks = 8192;   // covers N <= 8192 * 16384 cells
+constexpr int kMaxDevices = 64;
+
+// Block partials (4 doubles per block) followed by the 4 final sums. Every
+// slot a call reads is written earlier in the same call, so nothing needs
+// clearing between calls.
+static __device__ __align__(256) double g_moment_scratch[kStaticMomentBlocks * 4 + 4];
+
+std::mutex g_static_mu;
+double* g_static_scratch[kMaxDevices] = {};
+
+// Device address of g_moment_scratch on `dev`, looked up once per device with
+// that device current. The host-side name is only a stand-in for the symbol.
+int static_scratch(int dev, double** out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(LBM_ERR_UNSUPPORTED, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_scratch[dev]) {
+    int prev = -1;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e == cudaSuccess && prev != dev) e = cudaSetDevice(dev);
+    void* p = nullptr;
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&p, g_moment_scratch);
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_static_scratch[dev] = static_cast<double*>(p);
+  }
+  *out = g_static_scratch[dev];
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" int lbm_read_moments_noalloc(lbm_handle h, int32_t lattice, double out[4]) {
+  if (int rc = need_state(h, lattice)) return rc;
+  if (!out) return fail(LBM_ERR_ARG, "null output");
+  Lattice& L = h->lat[lattice];
+  const LatticeView v = L.view();
+  const int blocks = moments_blocks(v);
+  if (blocks > kStaticMomentBlocks)
+    return fail(LBM_ERR_ARG, "lattice too large for the static scratch of lbm_read_moments_noalloc: "
+                             "N must be <= 134217728 cells");
+  void* state = state_buffer(h, L);
+  cudaPointerAttributes attr{};
+  LBM_CUDA(h, cudaPointerGetAttributes(&attr, state), "device of the lattice");
+  double* scratch = nullptr;
+  if (int rc = static_scratch(attr.device, &scratch)) return rc;
+  double* d_out = scratch + (size_t)kStaticMomentBlocks * 4;
+  LBM_CUDA(h, launch_moments(v, current_layout(h), state, scratch, blocks, d_out, h->stream), "moments");
+  LBM_CUDA(h, cudaMemcpyAsync(out, d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy moments");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "moments sync");
+  return LBM_OK;
+}

@@ -84,6 +84,7 @@ def load(path: str | None = None):
         "lbm_read_macroscopic": [H, i32, vp, vp],
         "lbm_read_profile": [H, i32, i32, i32, vp, sz],
         "lbm_read_moments": [H, i32, vp],
+        "lbm_read_moments_noalloc": [H, i32, vp],
         "lbm_read_flags": [H, i32, vp, sz],
         "lbm_fluid_count": [H, i32, ctypes.POINTER(i64)],
         "lbm_read_adjacency": [H, i32, vp, sz],
@@ -266,6 +267,13 @@ def lbm_read_profile(h: Handle, lattice: int = 0, axis: int = 1, comp: int = 0) 
 def lbm_read_moments(h: Handle, lattice: int = 0) -> np.ndarray:
     out = np.empty(4)
     _check(load().lbm_read_moments(h, lattice, _ptr(out)))
+    return out
+
+
+def lbm_read_moments_noalloc(h: Handle, lattice: int = 0) -> np.ndarray:
+    """lbm_read_moments without device allocation (static scratch; see the header)."""
+    out = np.empty(4)
+    _check(load().lbm_read_moments_noalloc(h, lattice, _ptr(out)))
     return out
 
 
