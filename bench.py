@@ -32,6 +32,13 @@ from paper_1711_11468_gb300 import inputs  # noqa: E402
 
 WORKLOAD = inputs.DUCT_256
 DIMS = WORKLOAD["dims"]
+# FP64 pipe instructions per fluid lattice update of the FP64 AA sweep, from
+# ncu per-opcode counters (DADD 73, DFMA 57, DMUL 19 per fluid cell; see
+# profiles/dense_aa_f64_duct128_ncu.md), and the
+# FP64 pipe's rate on GB300 (2 per clock per SM at 2.07 GHz).
+FP64_INSTR_PER_FLUP = 149.0
+FP64_INSTR_PER_SEC = 152 * 2 * 2.07e9
+
 METRIC = "MFLUP/s and % of HBM roofline, FP64 vs FP32/FP16-shifted vs batched, at stated error"
 UNIT = "MFLUP/s"
 
@@ -174,6 +181,124 @@ def time_steps(lbm, h, steps, stream):
     return e0.elapsed_time(e1) / 1e3
 
 
+def make_porous(lbm, stream, precision, propagation, pack):
+    c = inputs.POROUS_256
+    desc = lbm.make_desc(c["dims"], precision, lbm.LBM_INDIRECT, propagation)
+    h = lbm.lbm_create_lattice(desc, stream)
+    lbm.lbm_set_geometry_spheres(h, 0, pack.spheres)
+    lbm.lbm_set_params(h, 0, c["omega"], c["Lambda"], c["force"])
+    lbm.lbm_init_equilibrium(h, 0)
+    return h
+
+
+def porous_variant(lbm, stream, precision, propagation, steps, pack, peak):
+    h = make_porous(lbm, stream, precision, propagation, pack)
+    try:
+        nf = lbm.lbm_fluid_count(h, 0)
+        lbm.lbm_autotune(h, 4)
+        lbm.lbm_step(h, 4)
+        sec = time_steps(lbm, h, steps, stream)
+    finally:
+        lbm.lbm_destroy(h)
+    mflups = nf * steps / sec / 1e6
+    elem = {lbm.LBM_F64: 8, lbm.LBM_F32_SHIFTED: 4, lbm.LBM_F16_SHIFTED: 2}[precision]
+    bpf = bytes_per_flup(elem, True, "pull" if propagation == lbm.LBM_PULL_TWO_GRID else "aa")
+    gbs = mflups * 1e6 * bpf / 1e9
+    return {"mflups": round(mflups, 1), "bytes_per_flup": bpf, "achieved_gbs": round(gbs, 1),
+            "roofline_frac": round(gbs / peak, 4), "steps": steps, "fluid_cells": nf,
+            "porosity": round(nf / float(np.prod(inputs.POROUS_256["dims"])), 4),
+            "workload": "porous 256^3, spheres r 4-12, fluid list + int32 adjacency, half-way bounce-back"}
+
+
+def batch_variant(lbm, stream, steps, peak):
+    """512 independent lattices (channels on full arrays, porous media on fluid
+    lists), FP32-shifted, one launch per step replayed from CUDA graphs."""
+    specs = inputs.batch_specs(**{k: v for k, v in inputs.BATCH_512.items() if k in ("count", "seed")})
+    descs = []
+    for sp in specs:
+        addr = lbm.LBM_DIRECT if sp.kind == "channel" else lbm.LBM_INDIRECT
+        per = (1, 0, 1) if sp.kind == "channel" else (1, 1, 1)
+        descs.append(lbm.make_desc(sp.dims, lbm.LBM_F32_SHIFTED, addr, lbm.LBM_AA_INPLACE, per))
+
+    def populate(h, k, sp, lattice):
+        if sp.kind == "channel":
+            lbm.lbm_set_geometry(h, lattice, sp.flags)
+        else:
+            lbm.lbm_set_geometry_spheres(h, lattice, sp.spheres)
+        lbm.lbm_set_params(h, lattice, sp.omega, sp.Lambda, sp.force)
+        lbm.lbm_init_equilibrium(h, lattice)
+
+    h = lbm.lbm_create_batch(descs, stream)
+    try:
+        for k, sp in enumerate(specs):
+            populate(h, k, sp, k)
+        nf = sum(lbm.lbm_fluid_count(h, k) for k in range(len(specs)))
+        ncells = sum(int(np.prod(sp.dims)) for sp in specs)
+        lbm.lbm_autotune(h, 6)
+        tuning = lbm.lbm_get_tuning(h)
+        lbm.lbm_step(h, 4)
+        sec = time_steps(lbm, h, steps, stream)
+        mem = lbm.lbm_memory_bytes(h)
+    finally:
+        lbm.lbm_destroy(h)
+    mflups = nf * steps / sec / 1e6
+    # one launch per lattice per step, for comparison
+    singles = [lbm.lbm_create_lattice(d, stream) for d in descs]
+    try:
+        for k, sp in enumerate(specs):
+            populate(singles[k], k, sp, 0)
+        import torch
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for hh in singles:
+            lbm.lbm_step(hh, 2)
+        torch.cuda.synchronize()
+        sk = max(2, steps // 5)
+        e0.record(stream)
+        for _ in range(sk):
+            for hh in singles:
+                lbm.lbm_step(hh, 1)
+        e1.record(stream)
+        e1.synchronize()
+        single_mflups = nf * sk / (e0.elapsed_time(e1) / 1e3) / 1e6
+    finally:
+        for hh in singles:
+            lbm.lbm_destroy(hh)
+    n_list = sum(1 for sp in specs if sp.kind != "channel")
+    # bytes per fluid update: dense channels 152 (+ their solid walls), lists 152 + 36 (AA)
+    return {"mflups": round(mflups, 1), "lattices": len(specs), "fluid_cells": nf, "cells": ncells,
+            "porous_lattices": n_list, "tuning": {"threads": tuning[0], "cells_per_thread": tuning[1],
+                                                  "ctas_per_sm": tuning[2]},
+            "one_launch_per_lattice_mflups": round(single_mflups, 1), "steps": steps,
+            "device_bytes": mem, "bytes_per_flup_range": [152.0, 188.0],
+            "roofline_frac_at_152": round(mflups * 1e6 * 152.0 / 1e9 / peak, 4)}
+
+
+def microbench(lbm, stream, elem: int = 8, n: int = 1 << 24, reps: int = 5):
+    """copy-19 and update-19 (Sec. 4.1) on 19 arrays of n elements: GB/s."""
+    import torch
+    stride = n
+    a = torch.empty(19 * stride * elem, dtype=torch.uint8, device="cuda")
+    b = torch.empty_like(a)
+    a.zero_()
+    b.zero_()
+    out = {}
+    for name in ("copy19", "update19"):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = 1e30
+        for _ in range(reps + 1):
+            e0.record(stream)
+            if name == "copy19":
+                lbm.lbm_bench_copy19(a.data_ptr(), b.data_ptr(), n, stride, elem, stream)
+            else:
+                lbm.lbm_bench_update19(a.data_ptr(), n, stride, elem, stream)
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        out[name + "_gbs"] = round(2 * 19 * n * elem / best / 1e9, 1)
+    del a, b
+    return out
+
+
 def variant(lbm, stream, precision, propagation, steps, nf, peak):
     h, _ = make_duct(lbm, stream, precision, propagation)
     try:
@@ -223,6 +348,8 @@ def run_gpu(args):
 
     h, flags = make_duct(lbm, stream, lbm.LBM_F64, lbm.LBM_AA_INPLACE)
     nf = int(np.count_nonzero(flags == 0))
+    lbm.lbm_autotune(h, 4)
+    threads = lbm.lbm_get_tuning(h)[0]
     lbm.lbm_step(h, args.warmup)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
@@ -259,11 +386,34 @@ def run_gpu(args):
     e2e_value = nf * args.steps * world / e2e_sec / 1e6
 
     variants = {}
+    micro = {}
     if rank == 0 and not args.no_variants:
         vs = min(args.steps, 200)
         variants["f64_pull_two_grid"] = variant(lbm, stream, lbm.LBM_F64, lbm.LBM_PULL_TWO_GRID, vs, nf, peak)
         variants["f32_shifted_aa"] = variant(lbm, stream, lbm.LBM_F32_SHIFTED, lbm.LBM_AA_INPLACE, vs, nf, peak)
         variants["f16_shifted_aa"] = variant(lbm, stream, lbm.LBM_F16_SHIFTED, lbm.LBM_AA_INPLACE, vs, nf, peak)
+        c2 = inputs.POROUS_256
+        pack = inputs.sphere_pack(c2["dims"], c2["seed"], c2["r_min"], c2["r_max"], c2["porosity"])
+        variants["f64_list_aa_porous256"] = porous_variant(lbm, stream, lbm.LBM_F64, lbm.LBM_AA_INPLACE, vs, pack,
+                                                           peak)
+        variants["f64_list_pull_porous256"] = porous_variant(lbm, stream, lbm.LBM_F64, lbm.LBM_PULL_TWO_GRID, vs,
+                                                             pack, peak)
+        variants["f32_list_aa_porous256"] = porous_variant(lbm, stream, lbm.LBM_F32_SHIFTED, lbm.LBM_AA_INPLACE, vs,
+                                                           pack, peak)
+        variants["f32_batched_512"] = batch_variant(lbm, stream, min(args.steps, 100), peak)
+        micro = microbench(lbm, stream)
+
+    # The FP64 sweep is bound by the FP64 pipe (2 FMA per clock per SM on GB300):
+    # its ALU roofline counts FP64 pipe instructions per fluid update (ncu).
+    fp64_rate = FP64_INSTR_PER_SEC
+    alu_achieved = value / world * 1e6 * FP64_INSTR_PER_FLUP
+    alu = {"bound": "alu", "achieved": round(alu_achieved / 1e9, 1), "peak": round(fp64_rate / 1e9, 1),
+           "unit": "G FP64 instr/s", "frac": round(alu_achieved / fp64_rate, 4), "traffic": None,
+           "instr_per_flup": FP64_INSTR_PER_FLUP,
+           "peak_source": "152 SMs x 2 FP64 FMA/clock x 2.07 GHz (FMA probe measured 598 G/s)"}
+    roofline = alu if alu["frac"] > achieved / peak else {
+        "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+        "frac": round(achieved / peak, 4), "traffic": None, "bytes_per_flup": bpf, "peak_source": peak_kind}
 
     if rank == 0:
         line = {
@@ -276,9 +426,12 @@ def run_gpu(args):
                        "dims": list(DIMS), "fluid_cells": nf, "omega": WORKLOAD["omega"],
                        "Lambda": WORKLOAD["Lambda"], "l2": "inputs larger than L2 (2.55 GB lattice)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": None,
-                         "bytes_per_flup": bpf, "peak_source": peak_kind},
+            "roofline": roofline,
+            "roofline_hbm": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                             "frac": round(achieved / peak, 4), "bytes_per_flup": bpf,
+                             "peak_source": peak_kind + " copy bandwidth"},
+            "microbench": micro,
+            "tuning": {"threads": threads},
             "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
                     "h2d_bytes_per_step": (N + 3 * N * 8) / args.steps,
                     "d2h_bytes_per_step": 4 * N * 8 / args.steps},

@@ -204,13 +204,18 @@ int lbm_fluid_count(lbm_handle h, int32_t lattice, int64_t* n_fluid);
  * Synchronous. */
 int lbm_read_adjacency(lbm_handle h, int32_t lattice, int32_t* out, size_t out_len);
 
-/* Kernel launch shape of the handle's sweep: threads per block and cells per
- * thread (the batch also uses the tile size in cells). lbm_set_tuning fixes
- * it (0 = keep); lbm_autotune times candidate shapes for `steps` steps each on
- * the handle's own data (state is saved and restored around the trials) and
- * keeps the fastest. Tuning is the launch-shape analogue of the paper's
- * search over blocking factors (Sec. 4.2, Sec. 4.3). */
-int lbm_set_tuning(lbm_handle h, int32_t threads, int32_t cells_per_thread, int32_t tile_cells);
+/* Kernel launch shape of the handle's sweep. threads: threads per block
+ * (multiple of 32 in [32, 512]); cells_per_thread: cells each thread takes per
+ * tile of a batch (1, 2, 4 or 8; single lattices use 1), so a tile holds
+ * threads*cells_per_thread cells; ctas_per_sm: for a batch, the persistent
+ * grid's CTAs per SM (0 = one CTA per tile instead of a persistent grid).
+ * lbm_set_tuning fixes the shape (a negative value keeps the current one);
+ * lbm_get_tuning returns {threads, cells_per_thread, ctas_per_sm}; lbm_autotune
+ * times candidate shapes for `steps` steps each on the handle's own data (the
+ * state is saved and restored around the trials) and keeps the fastest. The
+ * launch-shape search is the GPU analogue of the paper's search over blocking
+ * factors (Sec. 4.2, Sec. 4.3). */
+int lbm_set_tuning(lbm_handle h, int32_t threads, int32_t cells_per_thread, int32_t ctas_per_sm);
 int lbm_get_tuning(lbm_handle h, int32_t out[3]);
 int lbm_autotune(lbm_handle h, int32_t steps);
 

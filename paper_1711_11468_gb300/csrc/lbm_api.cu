@@ -72,7 +72,15 @@ struct lbm_lattice_s {
   int64_t steps = 0;     // since the last init / write
   int phase = 0;         // total steps mod 2: AA parity, pull buffer holding the state
   bool poisoned = false;
-  int threads = 256, cells_per_thread = 1, tile_cells = 0;
+  int threads = 256, cells_per_thread = 1, ctas_per_sm = 0;
+  // batch work list: one descriptor per lattice and the tiles (rebuilt lazily)
+  void* d_lat = nullptr;
+  size_t d_lat_bytes = 0;
+  BatchTile* d_tiles = nullptr;
+  size_t d_tiles_bytes = 0;
+  int ntiles = 0;
+  bool tables_dirty = true;
+  bool batched() const { return lat.size() > 1; }
   lbm_alloc_fn alloc = nullptr;
   lbm_free_fn free_ = nullptr;
   void* alloc_ctx = nullptr;
@@ -106,6 +114,15 @@ struct lbm_lattice_s {
       if (g) cudaGraphExecDestroy(g);
       g = nullptr;
     }
+    tables_dirty = true;
+  }
+  void free_tables() {
+    dfree(d_lat, d_lat_bytes);
+    dfree(d_tiles, d_tiles_bytes);
+    d_lat = nullptr;
+    d_tiles = nullptr;
+    d_lat_bytes = d_tiles_bytes = 0;
+    ntiles = 0;
   }
 };
 
@@ -304,8 +321,57 @@ int ready_to_step(lbm_handle h) {
   return LBM_OK;
 }
 
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+// (Re)build the batch descriptor table and the tile work list on the device.
+int build_tables(lbm_handle h) {
+  if (!h->tables_dirty) return LBM_OK;
+  h->free_tables();
+  const size_t db = batch_lattice_bytes(h->prec);
+  const int64_t tile = (int64_t)h->threads * h->cells_per_thread;
+  std::vector<unsigned char> desc(db * h->lat.size());
+  std::vector<BatchTile> tiles;
+  for (size_t k = 0; k < h->lat.size(); ++k) {
+    Lattice& L = h->lat[k];
+    fill_batch_lattice(h->prec, desc.data() + k * db, L.view(), L.pdf[0], L.pdf[1], L.trt);
+    for (int64_t first = 0; first < L.nstore; first += tile)
+      tiles.push_back(BatchTile{(int32_t)k, (int32_t)std::min<int64_t>(tile, L.nstore - first), first});
+  }
+  if (tiles.size() > (size_t)INT32_MAX) return fail(LBM_ERR_UNSUPPORTED, "too many tiles");
+  h->d_lat_bytes = desc.size();
+  h->d_tiles_bytes = std::max<size_t>(1, tiles.size()) * sizeof(BatchTile);
+  h->d_lat = h->dalloc(h->d_lat_bytes);
+  h->d_tiles = static_cast<BatchTile*>(h->dalloc(h->d_tiles_bytes));
+  if (!h->d_lat || !h->d_tiles) return fail(LBM_ERR_OOM, "allocation of the batch tables failed");
+  LBM_CUDA(h, cudaMemcpyAsync(h->d_lat, desc.data(), desc.size(), cudaMemcpyHostToDevice, h->stream), "copy table");
+  if (!tiles.empty())
+    LBM_CUDA(h, cudaMemcpyAsync(h->d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice,
+                                h->stream),
+             "copy tiles");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "table sync");
+  h->ntiles = (int)tiles.size();
+  h->tables_dirty = false;
+  return LBM_OK;
+}
+
+int batch_ctas(lbm_handle h, SweepKind kind) {
+  if (h->ctas_per_sm <= 0) return 0;
+  const int occ = batch_blocks_per_sm(h->prec, kind, h->threads);
+  return sm_count() * std::min(h->ctas_per_sm, occ);
+}
+
 // Launch one time step of every lattice on stream s, at phase `phase`.
 cudaError_t issue_step(lbm_handle h, int phase, cudaStream_t s) {
+  if (h->batched()) {
+    const SweepKind kind = h->prop == LBM_PULL_TWO_GRID ? kPull : (phase == 0 ? kAAEven : kAAOdd);
+    return launch_batch_sweep(h->prec, kind, h->d_lat, h->d_tiles, h->ntiles, h->threads, batch_ctas(h, kind), phase,
+                              s);
+  }
   for (Lattice& L : h->lat) {
     const LatticeView v = L.view();
     cudaError_t e;
@@ -336,6 +402,8 @@ cudaError_t capture_graph(lbm_handle h, int phase, cudaGraphExec_t* exec) {
 }
 
 int step_impl(lbm_handle h, int32_t n, bool use_graphs) {
+  if (h->batched())
+    if (int rc = build_tables(h)) return rc;
   int32_t done = 0;
   if (use_graphs) {
     while (n - done >= kGraphSteps) {
@@ -380,6 +448,7 @@ int lbm_destroy(lbm_handle h) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
   cudaStreamSynchronize(h->stream);
   h->drop_graphs();
+  h->free_tables();
   for (Lattice& L : h->lat) {
     free_storage(h, L);
     h->dfree(L.flags, (size_t)L.N);
@@ -602,16 +671,20 @@ int lbm_read_adjacency(lbm_handle h, int32_t lattice, int32_t* out, size_t out_l
   return LBM_OK;
 }
 
-int lbm_set_tuning(lbm_handle h, int32_t threads, int32_t cells_per_thread, int32_t tile_cells) {
+int lbm_set_tuning(lbm_handle h, int32_t threads, int32_t cells_per_thread, int32_t ctas_per_sm) {
   if (int rc = check_handle(h)) return rc;
-  if (threads != 0 && (threads < 32 || threads > 512 || threads % 32 != 0))
+  if (threads >= 0 && (threads < 32 || threads > 512 || threads % 32 != 0))
     return fail(LBM_ERR_ARG, "threads must be a multiple of 32 in [32, 512]");
-  if (cells_per_thread != 0 && cells_per_thread != 1) return fail(LBM_ERR_UNSUPPORTED, "cells_per_thread must be 1");
-  if (tile_cells < 0) return fail(LBM_ERR_ARG, "tile_cells must be >= 0");
+  if (cells_per_thread >= 0 && cells_per_thread != 1 && cells_per_thread != 2 && cells_per_thread != 4 &&
+      cells_per_thread != 8)
+    return fail(LBM_ERR_ARG, "cells_per_thread must be 1, 2, 4 or 8");
+  if (cells_per_thread > 1 && !h->batched())
+    return fail(LBM_ERR_UNSUPPORTED, "cells_per_thread > 1 applies to batches only");
+  if (ctas_per_sm > 64) return fail(LBM_ERR_ARG, "ctas_per_sm must be <= 64");
   h->drop_graphs();
-  if (threads) h->threads = threads;
-  if (cells_per_thread) h->cells_per_thread = cells_per_thread;
-  if (tile_cells) h->tile_cells = tile_cells;
+  if (threads >= 0) h->threads = threads;
+  if (cells_per_thread >= 0) h->cells_per_thread = cells_per_thread;
+  if (ctas_per_sm >= 0) h->ctas_per_sm = ctas_per_sm;
   return LBM_OK;
 }
 
@@ -620,7 +693,7 @@ int lbm_get_tuning(lbm_handle h, int32_t out[3]) {
   if (!out) return fail(LBM_ERR_ARG, "null output");
   out[0] = h->threads;
   out[1] = h->cells_per_thread;
-  out[2] = h->tile_cells;
+  out[2] = h->ctas_per_sm;
   return LBM_OK;
 }
 
@@ -644,13 +717,26 @@ int lbm_autotune(lbm_handle h, int32_t steps) {
                                 h->stream),
              "save state");
   }
-  const int candidates[] = {64, 128, 192, 256, 384, 512};
-  int best = h->threads;
+  struct Shape {
+    int threads, cpt, ctas;
+  };
+  std::vector<Shape> shapes;
+  if (h->batched()) {
+    for (int t : {128, 256, 512})
+      for (int c : {1, 2, 4, 8})
+        for (int g : {0, 2, 4, 8}) shapes.push_back({t, c, g});
+  } else {
+    for (int t : {64, 128, 192, 256, 384, 512}) shapes.push_back({t, 1, 0});
+  }
+  Shape best{h->threads, h->cells_per_thread, h->ctas_per_sm};
   float best_ms = 1e30f;
-  for (int t : candidates) {
-    h->threads = t;
+  int rc = LBM_OK;
+  for (const Shape& sh : shapes) {
     h->drop_graphs();
-    int rc = step_impl(h, 2, false);   // warm-up
+    h->threads = sh.threads;
+    h->cells_per_thread = sh.cpt;
+    h->ctas_per_sm = sh.ctas;
+    rc = step_impl(h, 2, false);   // warm-up (and table rebuild)
     if (rc == LBM_OK) {
       cudaEventRecord(h->ev0, h->stream);
       rc = step_impl(h, steps, false);
@@ -663,10 +749,12 @@ int lbm_autotune(lbm_handle h, int32_t steps) {
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     if (ms < best_ms) {
       best_ms = ms;
-      best = t;
+      best = sh;
     }
   }
-  h->threads = best;
+  h->threads = best.threads;
+  h->cells_per_thread = best.cpt;
+  h->ctas_per_sm = best.ctas;
   h->drop_graphs();
   h->phase = phase0;
   h->steps = steps0;
@@ -678,7 +766,8 @@ int lbm_autotune(lbm_handle h, int32_t steps) {
   }
   LBM_CUDA(h, cudaStreamSynchronize(h->stream), "autotune sync");
   for (size_t k = 0; k < h->lat.size(); ++k) h->dfree(saved[k], pdf_bytes(h->lat[k], h->prec));
-  return h->poisoned ? fail(LBM_ERR_CUDA, "autotune hit a CUDA error") : LBM_OK;
+  if (h->poisoned) return fail(LBM_ERR_CUDA, "autotune hit a CUDA error");
+  return rc;
 }
 
 int lbm_memory_bytes(lbm_handle h, int64_t* bytes) {

@@ -1,0 +1,184 @@
+// Batched sweep: many independent lattices (full arrays and fluid lists, each
+// with its own size, geometry and TRT parameters) advance by one time step in
+// a single launch. The work list is a sequence of tiles (lattice, first node,
+// count); a persistent grid of CTAs strides over it, or, with ctas = 0, one CTA
+// takes one tile. The per-node arithmetic is the single-lattice sweep's
+// (lbm_sweep.cuh). Not in the paper: its closest analogue is the OpenMP loop
+// over the fluid list (Sec. 3.1).
+#include "lbm_internal.h"
+#include "lbm_sweep.cuh"
+
+namespace lbm {
+
+template <typename S>
+Trt<Arith<S>> trt_as(const TrtParams& p);
+
+namespace {
+
+template <typename A>
+struct __align__(16) BatchDesc {
+  void* pdf[2];            // state grid(s): AA uses pdf[0]; pull alternates
+  const uint8_t* flags;    // [N], full array only
+  const int32_t* adj;      // [18][stride], fluid list only
+  int64_t stride;
+  int nx, ny, nz;
+  int indirect, has_halfway, small;   // small: N < 2^24 (fast coordinate split)
+  float inv_nx, inv_ny;
+  Trt<A> p;
+};
+
+// n -> (x, y, z) for a full array. For N < 2^24 the quotient through a float
+// reciprocal is off by at most one and is corrected; otherwise plain division.
+__device__ __forceinline__ void split_cell(int n, int nx, int ny, bool small, float inv_nx, float inv_ny, int& x,
+                                           int& y, int& z) {
+  int row, zz;
+  if (small) {
+    row = __float2int_rz(__int2float_rn(n) * inv_nx);
+    int r = n - row * nx;
+    while (r < 0) { --row; r += nx; }
+    while (r >= nx) { ++row; r -= nx; }
+    x = r;
+    zz = __float2int_rz(__int2float_rn(row) * inv_ny);
+    int r2 = row - zz * ny;
+    while (r2 < 0) { --zz; r2 += ny; }
+    while (r2 >= ny) { ++zz; r2 -= ny; }
+    y = r2;
+  } else {
+    row = n / nx;
+    x = n - row * nx;
+    zz = row / ny;
+    y = row - zz * ny;
+  }
+  z = zz;
+}
+
+template <typename S, int KIND>
+__global__ void __launch_bounds__(512) k_batch(const BatchDesc<Arith<S>>* __restrict__ lat,
+                                               const BatchTile* __restrict__ tiles, int ntiles, int phase) {
+  using A = Arith<S>;
+  using D = BatchDesc<A>;
+  __shared__ D sd;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const BatchTile tile = tiles[t];
+    __syncthreads();   // the previous tile is done with sd
+    {
+      const int4* src = reinterpret_cast<const int4*>(lat + tile.lattice);
+      int4* dst = reinterpret_cast<int4*>(&sd);
+      for (int w = threadIdx.x; w < (int)(sizeof(D) / sizeof(int4)); w += blockDim.x) dst[w] = src[w];
+    }
+    __syncthreads();
+    const int64_t stride = sd.stride;
+    for (int j = threadIdx.x; j < tile.count; j += blockDim.x) {
+      const int64_t node = tile.first + j;
+      if (sd.indirect) {
+        if (KIND == kPull)
+          pull_list_node<S>(static_cast<const S*>(sd.pdf[phase]), static_cast<S*>(sd.pdf[phase ^ 1]), sd.adj, node,
+                            stride, sd.p);
+        else if (KIND == kAAEven)
+          aa_even_node<S>(static_cast<S*>(sd.pdf[0]), node, stride, sd.p);
+        else
+          aa_odd_list_node<S>(static_cast<S*>(sd.pdf[0]), sd.adj, node, stride, sd.p);
+      } else {
+        const int n = (int)node;
+        if (KIND == kAAEven) {
+          if (sd.flags[n] == kFluid) aa_even_node<S>(static_cast<S*>(sd.pdf[0]), n, stride, sd.p);
+          continue;
+        }
+        int x, y, z;
+        split_cell(n, sd.nx, sd.ny, sd.small, sd.inv_nx, sd.inv_ny, x, y, z);
+        if (KIND == kPull) {
+          const S* src = static_cast<const S*>(sd.pdf[phase]);
+          S* dst = static_cast<S*>(sd.pdf[phase ^ 1]);
+          if (sd.has_halfway)
+            pull_dense_node<S, true>(src, dst, sd.flags, x, y, z, n, sd.nx, sd.ny, sd.nz, stride, sd.p);
+          else
+            pull_dense_node<S, false>(src, dst, sd.flags, x, y, z, n, sd.nx, sd.ny, sd.nz, stride, sd.p);
+        } else {
+          if (sd.flags[n] != kFluid) continue;
+          S* pdf = static_cast<S*>(sd.pdf[0]);
+          if (sd.has_halfway)
+            aa_odd_dense_node<S, true>(pdf, sd.flags, x, y, z, n, sd.nx, sd.ny, sd.nz, stride, sd.p);
+          else
+            aa_odd_dense_node<S, false>(pdf, sd.flags, x, y, z, n, sd.nx, sd.ny, sd.nz, stride, sd.p);
+        }
+      }
+    }
+  }
+}
+
+template <typename S>
+cudaError_t batch_typed(SweepKind kind, const void* d_lat, const BatchTile* d_tiles, int ntiles, int threads,
+                        int ctas, int phase, cudaStream_t s) {
+  using D = BatchDesc<Arith<S>>;
+  const D* lat = static_cast<const D*>(d_lat);
+  if (ntiles <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)(ctas > 0 ? std::min(ctas, ntiles) : ntiles);
+  switch (kind) {
+    case kPull: k_batch<S, kPull><<<grid, threads, 0, s>>>(lat, d_tiles, ntiles, phase); break;
+    case kAAEven: k_batch<S, kAAEven><<<grid, threads, 0, s>>>(lat, d_tiles, ntiles, phase); break;
+    case kAAOdd: k_batch<S, kAAOdd><<<grid, threads, 0, s>>>(lat, d_tiles, ntiles, phase); break;
+  }
+  return cudaGetLastError();
+}
+
+template <typename S>
+void fill_typed(void* host_desc, const LatticeView& v, void* pdf_a, void* pdf_b, const TrtParams& p) {
+  using D = BatchDesc<Arith<S>>;
+  D d{};
+  d.pdf[0] = pdf_a;
+  d.pdf[1] = pdf_b;
+  d.flags = v.flags;
+  d.adj = v.adj;
+  d.stride = v.stride;
+  d.nx = v.nx;
+  d.ny = v.ny;
+  d.nz = v.nz;
+  d.indirect = v.indirect ? 1 : 0;
+  d.has_halfway = v.has_halfway ? 1 : 0;
+  d.small = v.n_cells < (int64_t(1) << 24) ? 1 : 0;
+  d.inv_nx = 1.0f / (float)v.nx;
+  d.inv_ny = 1.0f / (float)v.ny;
+  d.p = trt_as<S>(p);
+  *static_cast<D*>(host_desc) = d;
+}
+
+}  // namespace
+
+size_t batch_lattice_bytes(int prec) {
+  return prec == kF64 ? sizeof(BatchDesc<double>) : sizeof(BatchDesc<float>);
+}
+
+void fill_batch_lattice(int prec, void* host_desc, const LatticeView& v, void* pdf_a, void* pdf_b,
+                        const TrtParams& p) {
+  switch (prec) {
+    case kF64: fill_typed<double>(host_desc, v, pdf_a, pdf_b, p); break;
+    case kF32: fill_typed<float>(host_desc, v, pdf_a, pdf_b, p); break;
+    default: fill_typed<__half>(host_desc, v, pdf_a, pdf_b, p); break;
+  }
+}
+
+int batch_blocks_per_sm(int prec, SweepKind kind, int threads) {
+  int n = 0;
+  cudaError_t e = cudaSuccess;
+#define LBM_OCC(S)                                                                                      \
+  switch (kind) {                                                                                       \
+    case kPull: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<S, kPull>, threads, 0); break; \
+    case kAAEven: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<S, kAAEven>, threads, 0); break; \
+    case kAAOdd: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<S, kAAOdd>, threads, 0); break; \
+  }
+  if (prec == kF64) { LBM_OCC(double) } else if (prec == kF32) { LBM_OCC(float) } else { LBM_OCC(__half) }
+#undef LBM_OCC
+  return e == cudaSuccess && n > 0 ? n : 1;
+}
+
+cudaError_t launch_batch_sweep(int prec, SweepKind kind, const void* d_lattices, const BatchTile* d_tiles,
+                               int32_t n_tiles, int threads, int ctas, int phase, cudaStream_t s) {
+  switch (prec) {
+    case kF64: return batch_typed<double>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, s);
+    case kF32: return batch_typed<float>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, s);
+    case kF16: return batch_typed<__half>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lbm

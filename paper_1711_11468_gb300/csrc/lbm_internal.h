@@ -54,6 +54,23 @@ cudaError_t launch_sweep(const LatticeView& v, SweepKind kind, const void* src, 
                          const TrtParams& p, int threads, cudaStream_t s);
 
 
+// One time step of every lattice of a batch in one launch. d_lattices holds one
+// descriptor per lattice (batch_lattice_bytes(prec) bytes each, filled by
+// fill_batch_lattice); d_tiles the work list. ctas > 0: a persistent grid of
+// that many CTAs strides over the tiles; ctas == 0: one CTA per tile.
+struct BatchTile {
+  int32_t lattice;
+  int32_t count;
+  int64_t first;
+};
+size_t batch_lattice_bytes(int prec);
+void fill_batch_lattice(int prec, void* host_desc, const LatticeView& v, void* pdf_a, void* pdf_b,
+                        const TrtParams& p);
+cudaError_t launch_batch_sweep(int prec, SweepKind kind, const void* d_lattices, const BatchTile* d_tiles,
+                               int32_t n_tiles, int threads, int ctas, int phase, cudaStream_t s);
+// Resident CTAs of the batched kernel per SM at this block size (occupancy).
+int batch_blocks_per_sm(int prec, SweepKind kind, int threads);
+
 // ------------------------------------------------------- state conversions
 // Write storage `dst` in `layout` from canonical FP64 values, which come either
 // from a device array canon[19][N] (non-null) or, if canon is null, from the

@@ -51,11 +51,15 @@ static_assert(table_ok(), "D3Q19 direction table does not match the ABI order");
 
 enum Flag : uint8_t { kFluid = 0, kSolidFullway = 1, kSolidHalfway = 2 };
 
-// TRT parameters in the arithmetic type A. fk[k-1] = 3 w_k (c_k . F) is the
-// body-force source of direction k (its opposite gets -fk).
+// TRT parameters in the arithmetic type A, folded for the pair update below:
+//   a = (1 - w+)/2, b = (1 - w-)/2, wp_w[c] = w+ * w_c, c4[c] = 9/2 w+ w_c,
+//   c3[c] = 3 w- w_c for the weight classes c = 0 (faces), 1 (edges),
+//   fk[k-1] = 3 w_k (c_k . F) the body-force source of direction k (its
+//   opposite gets -fk), rest = 1 - w+, wp_w0 = w+ / 3.
 template <typename A>
 struct Trt {
-  A omega_p, omega_m;
+  A a, b, rest, wp_w0;
+  A wp_w[2], c4[2], c3[2];
   A fk[9];
 };
 
@@ -109,9 +113,14 @@ struct Storage<__half> {
 //   e_i = w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u),
 //   per pair (k, k+9): f+ = (f_k + f_k+9)/2, f- = (f_k - f_k+9)/2 (same for e),
 //   f*_k = f_k - w+ (f+ - e+) - w- (f- - e-) + 3 w_k c_k.F, f*_k+9 mirrored.
+// Written per pair with s = f_k + f_k+9 and d = f_k - f_k+9 as
+//   P = (1 - w+) s/2 + w+ e+,  M = (1 - w-) d/2 + w- e- + 3 w_k c_k.F,
+//   f*_k = P + M,  f*_k+9 = P - M,
+// with e+ = w (rho - 3/2 rho u.u) + 9/2 w (c.u)(c.j) and e- = 3 w (c.j): the same
+// algebra, arranged so that each step is a fused multiply-add.
 // With kShifted, f holds d_i = f_i - w_i: then rho = 1 + sum d_i, j = sum c_i d_i
 // (sum c_i w_i = 0), and e_i - w_i = w_i (drho - 3/2 rho u.u + 3 c.j + 9/2 (c.u)(c.j)),
-// which is the same pairwise algebra with rho replaced by drho in the constant term.
+// the same pairwise algebra with rho replaced by drho in the constant term.
 template <typename A, bool kShifted>
 __device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
   A s[10], d[10];
@@ -128,26 +137,21 @@ __device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
   const A inv_rho = A(1) / rho;
   const A ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
   const A usq = ux * ux + uy * uy + uz * uz;
-  // constant part of e+ per weight: w (rho0 - 3/2 rho u.u)
-  const A base = rho0 - A(1.5) * rho * usq;
-  constexpr A w0 = A(1.0 / 3.0), wf = A(1.0 / 18.0), we = A(1.0 / 36.0);
-  const A base_f = wf * base, base_e = we * base;
-  const A half = A(0.5);
+  // constant part of e+ per unit weight: rho0 - 3/2 rho u.u
+  const A base = rho0 - A(1.5) * (rho * usq);
+  const A bw[2] = {p.wp_w[0] * base, p.wp_w[1] * base};   // w+ w_c base
 
-  // rest direction: only the symmetric part relaxes
-  f[0] = f[0] - p.omega_p * (f[0] - w0 * base);
+  f[0] = p.rest * f[0] + p.wp_w0 * base;
 
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
+    const int c = k <= 3 ? 0 : 1;
     const A cu = A(cx(k)) * ux + A(cy(k)) * uy + A(cz(k)) * uz;
     const A cj = A(cx(k)) * jx + A(cy(k)) * jy + A(cz(k)) * jz;
-    const A w = (k <= 3) ? wf : we;
-    const A eplus = ((k <= 3) ? base_f : base_e) + (A(4.5) * w) * (cu * cj);
-    const A eminus = (A(3) * w) * cj;
-    const A dplus = p.omega_p * (half * s[k] - eplus);
-    const A dminus = p.omega_m * (half * d[k] - eminus) - p.fk[k - 1];
-    f[k] = f[k] - dplus - dminus;
-    f[k + 9] = f[k + 9] - dplus + dminus;
+    const A P = p.c4[c] * (cu * cj) + (p.a * s[k] + bw[c]);
+    const A M = p.b * d[k] + (p.c3[c] * cj + p.fk[k - 1]);
+    f[k] = P + M;
+    f[k + 9] = P - M;
   }
 }
 

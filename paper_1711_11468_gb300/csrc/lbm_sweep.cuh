@@ -1,0 +1,176 @@
+// Per-node bodies of the fused collide-and-propagate sweep (Sec. 3 of
+// arXiv 1711.11468), shared by the single-lattice kernels and the batched
+// kernel. Structure-of-arrays storage: direction i of node n at pdf[i*stride + n].
+//
+//   pull (two grids, Table 1 "pull-soa" / "list-pull-soa"): gather f_i from
+//     slot i of x - c_i in src, collide, write slot i of x in dst.
+//   AA even (one grid, Table 1 "aa-soa" / "list-aa-soa"): read slot i of x,
+//     collide, write the result of direction i into slot opp(i) of x.
+//   AA odd: gather slot opp(i) of x - c_i, collide, scatter into slot i of
+//     x + c_i. Each node writes exactly the slots it read, so the in-place
+//     update is race-free (Sec. 3 "AA Pattern Kernels").
+// Bounce-back (Sec. 2, Sec. 3.2) is fused: a link into a half-way solid cell
+// reflects into the node's own opposite slot (the list encodes it as adj = -1);
+// a full-way solid cell reverses its populations in the pull sweep and needs no
+// work at all in the AA sweep, where the reversed population is the one already
+// parked in its slot.
+#pragma once
+
+#include "lbm_model.cuh"
+
+namespace lbm {
+
+template <typename S>
+using Arith = typename Storage<S>::A;
+
+// Wrapped neighbour offsets of one cell of a full array.
+struct Nbr {
+  int xm, xp, ym, yp, zm, zp;  // offsets to x-1, x+1, y-1, y+1, z-1, z+1
+  __device__ __forceinline__ Nbr(int x, int y, int z, int nx, int ny, int nz) {
+    const int plane = nx * ny;
+    xm = (x == 0) ? nx - 1 : -1;
+    xp = (x == nx - 1) ? 1 - nx : 1;
+    ym = (y == 0) ? (ny - 1) * nx : -nx;
+    yp = (y == ny - 1) ? -(ny - 1) * nx : nx;
+    zm = (z == 0) ? (nz - 1) * plane : -plane;
+    zp = (z == nz - 1) ? -(nz - 1) * plane : plane;
+  }
+  // offset to the upstream cell x - c_i
+  __device__ __forceinline__ int up(int i) const {
+    return (cx(i) > 0 ? xm : (cx(i) < 0 ? xp : 0)) + (cy(i) > 0 ? ym : (cy(i) < 0 ? yp : 0)) +
+           (cz(i) > 0 ? zm : (cz(i) < 0 ? zp : 0));
+  }
+  // offset to the downstream cell x + c_i
+  __device__ __forceinline__ int down(int i) const { return up(opp(i)); }
+};
+
+template <typename S>
+__device__ __forceinline__ const S* dir(const S* base, int i, int64_t stride) {
+  return base + (int64_t)i * stride;
+}
+template <typename S>
+__device__ __forceinline__ S* dir(S* base, int i, int64_t stride) {
+  return base + (int64_t)i * stride;
+}
+
+template <typename A>
+__device__ __forceinline__ void reverse(A (&f)[Q]) {
+#pragma unroll
+  for (int k = 1; k <= 9; ++k) {
+    const A t = f[k];
+    f[k] = f[k + 9];
+    f[k + 9] = t;
+  }
+}
+
+// ------------------------------------------------------------- full array
+template <typename S, bool kHW>
+__device__ __forceinline__ void pull_dense_node(const S* __restrict__ src, S* __restrict__ dst,
+                                                const uint8_t* __restrict__ flags, int x, int y, int z, int n,
+                                                int nx, int ny, int nz, int64_t stride, const Trt<Arith<S>>& p) {
+  using A = Arith<S>;
+  const uint8_t fl = flags[n];
+  if (fl == kSolidHalfway) return;
+  const Nbr nb(x, y, z, nx, ny, nz);
+  A f[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int m = n + nb.up(i);
+    if (kHW && i != 0 && flags[m] == kSolidHalfway)
+      f[i] = Storage<S>::load(dir(src, opp(i), stride) + n);
+    else
+      f[i] = Storage<S>::load(dir(src, i, stride) + m);
+  }
+  if (fl == kSolidFullway)
+    reverse(f);
+  else
+    collide<A, Storage<S>::kShifted>(f, p);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + n, f[i]);
+}
+
+// Node-local even step; the caller skips nodes that are not fluid.
+template <typename S>
+__device__ __forceinline__ void aa_even_node(S* __restrict__ pdf, int64_t k, int64_t stride,
+                                             const Trt<Arith<S>>& p) {
+  using A = Arith<S>;
+  A f[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) f[i] = Storage<S>::load(dir(pdf, i, stride) + k);
+  collide<A, Storage<S>::kShifted>(f, p);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) Storage<S>::store(dir(pdf, opp(i), stride) + k, f[i]);
+}
+
+// Odd step at fluid cell n of a full array; the caller skips solid cells.
+template <typename S, bool kHW>
+__device__ __forceinline__ void aa_odd_dense_node(S* __restrict__ pdf, const uint8_t* __restrict__ flags, int x,
+                                                  int y, int z, int n, int nx, int ny, int nz, int64_t stride,
+                                                  const Trt<Arith<S>>& p) {
+  using A = Arith<S>;
+  const Nbr nb(x, y, z, nx, ny, nz);
+  A f[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int m = n + nb.up(i);
+    if (kHW && i != 0 && flags[m] == kSolidHalfway)
+      f[i] = Storage<S>::load(dir(pdf, i, stride) + n);
+    else
+      f[i] = Storage<S>::load(dir(pdf, opp(i), stride) + m);
+  }
+  collide<A, Storage<S>::kShifted>(f, p);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int m = n + nb.down(i);
+    if (kHW && i != 0 && flags[m] == kSolidHalfway)
+      Storage<S>::store(dir(pdf, opp(i), stride) + n, f[i]);
+    else
+      Storage<S>::store(dir(pdf, i, stride) + m, f[i]);
+  }
+}
+
+// ------------------------------------------------------------ fluid list
+// adj[(i-1)*stride + k] = list index of the upstream node x_k - c_i, or -1.
+template <typename S>
+__device__ __forceinline__ void pull_list_node(const S* __restrict__ src, S* __restrict__ dst,
+                                               const int32_t* __restrict__ adj, int64_t k, int64_t stride,
+                                               const Trt<Arith<S>>& p) {
+  using A = Arith<S>;
+  A f[Q];
+  f[0] = Storage<S>::load(src + k);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int32_t a = __ldg(adj + (int64_t)(i - 1) * stride + k);
+    f[i] = a >= 0 ? Storage<S>::load(dir(src, i, stride) + a) : Storage<S>::load(dir(src, opp(i), stride) + k);
+  }
+  collide<A, Storage<S>::kShifted>(f, p);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + k, f[i]);
+}
+
+template <typename S>
+__device__ __forceinline__ void aa_odd_list_node(S* __restrict__ pdf, const int32_t* __restrict__ adj, int64_t k,
+                                                 int64_t stride, const Trt<Arith<S>>& p) {
+  using A = Arith<S>;
+  int32_t a[Q];
+  a[0] = (int32_t)k;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) a[i] = __ldg(adj + (int64_t)(i - 1) * stride + k);
+  A f[Q];
+  f[0] = Storage<S>::load(pdf + k);
+#pragma unroll
+  for (int i = 1; i < Q; ++i)
+    f[i] = a[i] >= 0 ? Storage<S>::load(dir(pdf, opp(i), stride) + a[i]) : Storage<S>::load(dir(pdf, i, stride) + k);
+  collide<A, Storage<S>::kShifted>(f, p);
+  Storage<S>::store(pdf + k, f[0]);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int32_t dn = a[opp(i)];   // downstream node x_k + c_i
+    if (dn >= 0)
+      Storage<S>::store(dir(pdf, i, stride) + dn, f[i]);
+    else
+      Storage<S>::store(dir(pdf, opp(i), stride) + k, f[i]);
+  }
+}
+
+}  // namespace lbm

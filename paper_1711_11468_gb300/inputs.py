@@ -91,6 +91,69 @@ class SpherePack:
     est_solid_fraction: float    # Monte Carlo estimate used as the stopping rule
 
 
+class _Coverage:
+    """Monte Carlo estimate of the solid fraction of a growing set of spheres:
+    which of `pts` (random points in continuous space) lie inside any sphere
+    added so far. Points are bucketed on a coarse grid so that a sphere only
+    tests the points near it. Spheres are added one at a time, in order; add()
+    reports how many to keep so that the set stops at the first sphere that
+    makes the covered count reach `target`."""
+
+    def __init__(self, pts: np.ndarray, box: np.ndarray, bucket: int = 8):
+        self.box = box.astype(np.float64)
+        self.nb = np.maximum(1, box // bucket).astype(np.int64)
+        self.edge = self.box / self.nb
+        cell = np.minimum((pts / self.edge).astype(np.int64), self.nb - 1)
+        bid = cell[:, 0] + self.nb[0] * (cell[:, 1] + self.nb[1] * cell[:, 2])
+        order = np.argsort(bid, kind="stable")
+        self.pts = pts[order]
+        nbt = int(np.prod(self.nb))
+        self.start = np.searchsorted(bid[order], np.arange(nbt + 1))
+        self.covered = np.zeros(len(pts), dtype=bool)
+        self.count = 0
+
+    def _axis_buckets(self, a: int, c: float, r: float) -> np.ndarray:
+        lo = int(np.floor((c - r) / self.edge[a]))
+        hi = int(np.floor((c + r) / self.edge[a]))
+        if hi - lo + 1 >= self.nb[a]:
+            return np.arange(self.nb[a])
+        return np.arange(lo, hi + 1) % self.nb[a]
+
+    def add(self, centres: np.ndarray, radii: np.ndarray, target: int):
+        for k in range(len(radii)):
+            c = centres[k].astype(np.float64)
+            r = float(radii[k])
+            bx, by, bz = (self._axis_buckets(a, c[a], r) for a in range(3))
+            ids = (bx[None, None, :] + self.nb[0] * (by[None, :, None] + self.nb[1] * bz[:, None, None])).ravel()
+            lens = self.start[ids + 1] - self.start[ids]
+            tot = int(lens.sum())
+            if tot:
+                base = np.repeat(self.start[ids] - np.concatenate([[0], np.cumsum(lens)[:-1]]), lens)
+                idx = base + np.arange(tot)
+                idx = idx[~self.covered[idx]]
+                d = self.pts[idx] - c
+                d -= self.box * np.round(d / self.box)
+                hit = idx[(d * d).sum(1) <= r * r]
+                self.covered[hit] = True
+                self.count += hit.size
+            if self.count >= target:
+                return k + 1, True
+        return len(radii), False
+
+
+def _clashes(ca, ra, cb, rb, box, gap) -> np.ndarray:
+    """[len(ra), len(rb)] True where two spheres come closer than r1 + r2 + gap
+    (minimum image; exact: integer coordinates in float32)."""
+    d2 = np.zeros((len(ra), len(rb)), dtype=np.float32)
+    for a in range(3):
+        d = ca[:, a, None].astype(np.float32) - cb[None, :, a].astype(np.float32)
+        L = np.float32(box[a])
+        d -= L * np.round(d / L)
+        d2 += d * d
+    lim = (ra[:, None] + rb[None, :] + gap).astype(np.float32)
+    return d2 < lim * lim
+
+
 def sphere_pack(dims, seed: int, r_min: int, r_max: int, porosity: float,
                 nonoverlap_attempts: int = 50_000, mc_points: int = 200_000,
                 gap: int = 1) -> SpherePack:
@@ -98,71 +161,55 @@ def sphere_pack(dims, seed: int, r_min: int, r_max: int, porosity: float,
 
     Phase 1 places non-overlapping spheres by random sequential addition
     (centre distance >= r1 + r2 + gap, minimum image) for a fixed number of
-    attempts. Phase 2 keeps adding spheres with overlap allowed until the
-    estimated solid fraction reaches 1 - porosity. The estimate is a Monte
-    Carlo count over `mc_points` random points in continuous space; the exact
-    porosity is whatever the voxelisation gives, and callers record it.
+    attempts, drawn in batches of 2048 and accepted in draw order. Phase 2 keeps
+    adding spheres with overlap allowed. Both phases stop at the first sphere
+    after which the estimated solid fraction reaches 1 - porosity; the estimate
+    is a Monte Carlo count over `mc_points` random points in continuous space.
+    The exact porosity is whatever the voxelisation gives; callers record it.
     """
     nx, ny, nz = dims
     box = np.array([nx, ny, nz], dtype=np.int64)
     rng = np.random.Generator(np.random.PCG64(seed))
-    target = 1.0 - porosity
     pts = rng.random((mc_points, 3)) * box
-    inside = np.zeros(mc_points, dtype=bool)
-
-    def cover(c, r):
-        d = pts - c
-        d -= box * np.round(d / box)
-        inside[(d * d).sum(1) <= float(r) * float(r)] = True
+    cov = _Coverage(pts, box)
+    target = int(math.ceil((1.0 - porosity) * mc_points))
 
     placed_c = np.empty((0, 3), dtype=np.int64)
     placed_r = np.empty(0, dtype=np.int64)
     attempts = 0
-    batch = 2048
-    while attempts < nonoverlap_attempts and inside.mean() < target:
-        m = min(batch, nonoverlap_attempts - attempts)
+    done = cov.count >= target
+    while attempts < nonoverlap_attempts and not done:
+        m = min(2048, nonoverlap_attempts - attempts)
         cand_c = np.stack([rng.integers(0, n, m) for n in (nx, ny, nz)], 1).astype(np.int64)
         cand_r = rng.integers(r_min, r_max + 1, m).astype(np.int64)
         attempts += m
         if placed_r.size:
-            d = cand_c[:, None, :] - placed_c[None, :, :]
-            d = (d + box // 2) % box - box // 2
-            d2 = (d * d).sum(2)
-            lim = cand_r[:, None] + placed_r[None, :] + gap
-            ok = ~(d2 < lim * lim).any(1)
+            ok = ~_clashes(cand_c, cand_r, placed_c, placed_r, box, gap).any(1)
         else:
             ok = np.ones(m, dtype=bool)
-        acc_c, acc_r = [], []
-        for k in np.nonzero(ok)[0]:
-            c, r = cand_c[k], cand_r[k]
-            good = True
-            for c2, r2 in zip(acc_c, acc_r):
-                d = (c - c2 + box // 2) % box - box // 2
-                if int((d * d).sum()) < (r + r2 + gap) ** 2:
-                    good = False
-                    break
-            if good:
-                acc_c.append(c)
-                acc_r.append(r)
-                cover(c, r)
-                if inside.mean() >= target:
-                    break
-        if acc_r:
-            placed_c = np.concatenate([placed_c, np.array(acc_c)])
-            placed_r = np.concatenate([placed_r, np.array(acc_r)])
+        idx = np.nonzero(ok)[0]
+        c, r = cand_c[idx], cand_r[idx]
+        clash = _clashes(c, r, c, r, box, gap)
+        np.fill_diagonal(clash, False)
+        keep = np.zeros(len(r), dtype=bool)
+        for k in range(len(r)):             # greedy, in draw order
+            keep[k] = not (clash[k] & keep).any()
+        c, r = c[keep], r[keep]
+        n_keep, done = cov.add(c, r, target)
+        placed_c = np.concatenate([placed_c, c[:n_keep]])
+        placed_r = np.concatenate([placed_r, r[:n_keep]])
     n_nonoverlap = placed_r.size
-    extra_c, extra_r = [], []
-    while inside.mean() < target:
-        c = np.array([rng.integers(0, n) for n in (nx, ny, nz)], dtype=np.int64)
-        r = int(rng.integers(r_min, r_max + 1))
-        extra_c.append(c)
-        extra_r.append(r)
-        cover(c, r)
-    if extra_r:
-        placed_c = np.concatenate([placed_c, np.array(extra_c)])
-        placed_r = np.concatenate([placed_r, np.array(extra_r)])
+    n_overlap = 0
+    while not done:
+        m = 256
+        c = np.stack([rng.integers(0, n, m) for n in (nx, ny, nz)], 1).astype(np.int64)
+        r = rng.integers(r_min, r_max + 1, m).astype(np.int64)
+        n_keep, done = cov.add(c, r, target)
+        placed_c = np.concatenate([placed_c, c[:n_keep]])
+        placed_r = np.concatenate([placed_r, r[:n_keep]])
+        n_overlap += n_keep
     spheres = np.concatenate([placed_c, placed_r[:, None]], 1).astype(np.int32)
-    return SpherePack(spheres, n_nonoverlap, len(extra_r), float(inside.mean()))
+    return SpherePack(spheres, n_nonoverlap, n_overlap, cov.count / mc_points)
 
 
 @dataclass

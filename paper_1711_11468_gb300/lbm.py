@@ -296,8 +296,9 @@ def lbm_read_adjacency(h: Handle, lattice: int = 0) -> np.ndarray:
     return out
 
 
-def lbm_set_tuning(h: Handle, threads: int = 0, cells_per_thread: int = 0, tile_cells: int = 0):
-    _check(load().lbm_set_tuning(h, threads, cells_per_thread, tile_cells))
+def lbm_set_tuning(h: Handle, threads: int = -1, cells_per_thread: int = -1, ctas_per_sm: int = -1):
+    """Negative values keep the current setting."""
+    _check(load().lbm_set_tuning(h, threads, cells_per_thread, ctas_per_sm))
 
 
 def lbm_get_tuning(h: Handle):

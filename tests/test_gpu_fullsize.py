@@ -1,0 +1,135 @@
+"""Parity at the benchmark's full sizes, in the benchmark's launch configuration.
+
+After k steps a cell depends only on the cells within k lattice steps of it
+(D3Q19 moves at most one cell per axis per step). So the oracle can compute
+sampled outputs of a 256^3 run one by one: it runs k push steps on the
+(2k+3)^3 block around the sample, cut out of the full lattice with periodic
+indexing and treated as a periodic box of its own; wrapping errors start at the
+block's faces and travel one cell per step, so they never reach the centre.
+"""
+import numpy as np
+import pytest
+
+from paper_1711_11468_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+LAM = 3.0 / 16.0
+
+
+def sample_cells(dims, n, seed, extra=()):
+    rng = np.random.default_rng(seed)
+    pts = [tuple(int(rng.integers(0, d)) for d in dims) for _ in range(n)]
+    return list(extra) + pts
+
+
+def block_indices(dims, c, R):
+    nx, ny, nz = dims
+    xs = (c[0] + np.arange(-R, R + 1)) % nx
+    ys = (c[1] + np.arange(-R, R + 1)) % ny
+    zs = (c[2] + np.arange(-R, R + 1)) % nz
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    return (X + nx * (Y + ny * Z)).reshape(-1)
+
+
+def cone_oracle(orc, dims, flags, u, c, steps, omega, F):
+    R = steps + 1
+    idx = block_indices(dims, c, R)
+    sub = (2 * R + 1,) * 3
+    fl = flags[idx]
+    f0 = orc.init_equilibrium(sub, fl, None, u[:, idx])
+    f = orc.run(sub, fl, omega, orc.omega_minus(omega, LAM), F, f0, steps, 1)
+    centre = R + sub[0] * (R + sub[1] * R)
+    return f[:, centre]
+
+
+def gpu_full(lbm, dims, prec, addr, prop, steps, omega, F, flags=None, spheres=None, u=None, periodic=(1, 1, 1),
+             autotune=False):
+    import torch
+    h = lbm.lbm_create_lattice(lbm.make_desc(dims, prec, addr, prop, periodic), torch.cuda.current_stream())
+    try:
+        if spheres is not None:
+            lbm.lbm_set_geometry_spheres(h, 0, spheres)
+        else:
+            lbm.lbm_set_geometry(h, 0, flags)
+        lbm.lbm_set_params(h, 0, omega, LAM, F)
+        lbm.lbm_init_equilibrium(h, 0, None, u)
+        if autotune:
+            lbm.lbm_autotune(h, 4)
+        lbm.lbm_step(h, steps)
+        return lbm.lbm_read_pdfs(h, 0), lbm.lbm_read_flags(h, 0), lbm.lbm_read_moments(h, 0)
+    finally:
+        lbm.lbm_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def duct():
+    c = inputs.DUCT_256
+    dims = c["dims"]
+    flags = inputs.duct_flags(*dims)
+    u = inputs.velocity_perturbation(*dims, seed=c["seed"], amplitude=c["amplitude"], flags=flags)
+    return c, dims, flags, u
+
+
+@pytest.mark.parametrize("prop", [1, 0])
+@pytest.mark.parametrize("steps", [2, 3])
+def test_duct256_lightcone(lbm, orc, duct, prop, steps):
+    c, dims, flags, u = duct
+    got, _, _ = gpu_full(lbm, dims, 0, 0, prop, steps, c["omega"], c["force"], flags=flags, u=u,
+                         periodic=(1, 0, 0), autotune=(prop == 1))
+    corners = [(0, 0, 0), (255, 1, 1), (17, 254, 254), (128, 1, 200), (3, 128, 254)]
+    for cell in sample_cells(dims, 40, 21 + steps, corners):
+        n = cell[0] + dims[0] * (cell[1] + dims[1] * cell[2])
+        ref = cone_oracle(orc, dims, flags, u, cell, steps, c["omega"], c["force"])
+        assert np.abs(got[:, n] - ref).max() <= 1e-14, cell
+
+
+def test_duct256_1000_steps_mass_and_aa_equals_pull(lbm, duct):
+    c, dims, flags, u = duct
+    a, _, ma = gpu_full(lbm, dims, 0, 0, 1, 1000, c["omega"], c["force"], flags=flags, u=u, periodic=(1, 0, 0),
+                        autotune=True)
+    b, _, mb = gpu_full(lbm, dims, 0, 0, 0, 1000, c["omega"], c["force"], flags=flags, u=u, periodic=(1, 0, 0))
+    assert np.array_equal(a, b)
+    N = flags.size
+    rho0 = 1.0 * N   # equilibrium at rho = 1 in every cell holding PDFs (walls included)
+    assert abs(ma[0] - rho0) / rho0 <= 1e-13
+    assert abs(mb[0] - rho0) / rho0 <= 1e-13
+
+
+@pytest.fixture(scope="module")
+def porous():
+    c = inputs.POROUS_256
+    dims = c["dims"]
+    pack = inputs.sphere_pack(dims, c["seed"], c["r_min"], c["r_max"], c["porosity"])
+    return c, dims, pack
+
+
+def brute_flags(dims, spheres, cells):
+    nx, ny, nz = dims
+    cells = np.asarray(cells)
+    x, y, z = cells % nx, (cells // nx) % ny, cells // (nx * ny)
+    inside = np.zeros(len(cells), dtype=bool)
+    for cx, cy, cz, r in spheres:
+        dx = np.minimum((x - cx) % nx, (cx - x) % nx)
+        dy = np.minimum((y - cy) % ny, (cy - y) % ny)
+        dz = np.minimum((z - cz) % nz, (cz - z) % nz)
+        inside |= dx * dx + dy * dy + dz * dz <= r * r
+    return np.where(inside, 2, 0).astype(np.uint8)
+
+
+@pytest.mark.parametrize("prop", [1, 0])
+def test_porous256_lightcone(lbm, orc, porous, prop):
+    c, dims, pack = porous
+    steps = 3
+    got, gflags, _ = gpu_full(lbm, dims, 0, 1, prop, steps, c["omega"], c["force"], spheres=pack.spheres)
+    porosity = float(np.count_nonzero(gflags == 0)) / gflags.size
+    assert 0.55 <= porosity <= 0.65, porosity
+    u = np.zeros((3, gflags.size))
+    for cell in sample_cells(dims, 24, 77):
+        R = steps + 1
+        idx = block_indices(dims, cell, R)
+        fl = brute_flags(dims, pack.spheres, idx)       # independent of the device voxelisation
+        assert np.array_equal(gflags[idx], fl)
+        n = cell[0] + dims[0] * (cell[1] + dims[1] * cell[2])
+        ref = cone_oracle(orc, dims, gflags, u, cell, steps, c["omega"], c["force"])
+        assert np.abs(got[:, n] - ref).max() <= 1e-14, cell

@@ -23,7 +23,7 @@ def gpu_run(lbm, dims, *, flags=None, spheres=None, prec=0, addr=0, prop=1, omeg
     h = lbm.lbm_create_lattice(desc, torch.cuda.current_stream())
     try:
         if threads:
-            lbm.lbm_set_tuning(h, threads, 0, 0)
+            lbm.lbm_set_tuning(h, threads)
         if spheres is not None:
             lbm.lbm_set_geometry_spheres(h, 0, spheres)
         else:
