@@ -302,12 +302,13 @@ def microbench(lbm, stream, elem: int = 8, n: int = 1 << 24, reps: int = 5):
 def variant(lbm, stream, precision, propagation, steps, nf, peak):
     h, _ = make_duct(lbm, stream, precision, propagation)
     try:
+        lbm.lbm_autotune(h, 4)
         lbm.lbm_step(h, 4)
         sec = time_steps(lbm, h, steps, stream)
     finally:
         lbm.lbm_destroy(h)
     mflups = nf * steps / sec / 1e6
-    elem = {lbm.LBM_F64: 8, lbm.LBM_F32_SHIFTED: 4, lbm.LBM_F16_SHIFTED: 2}[precision]
+    elem = {lbm.LBM_F64: 8, lbm.LBM_F32_SHIFTED: 4, lbm.LBM_F16_SHIFTED: 2, lbm.LBM_F64_DOUBLE_FLOAT: 8}[precision]
     bpf = bytes_per_flup(elem, False, "pull" if propagation == lbm.LBM_PULL_TWO_GRID else "aa")
     gbs = mflups * 1e6 * bpf / 1e9
     return {"mflups": round(mflups, 1), "bytes_per_flup": bpf, "achieved_gbs": round(gbs, 1),
@@ -390,6 +391,10 @@ def run_gpu(args):
     if rank == 0 and not args.no_variants:
         vs = min(args.steps, 200)
         variants["f64_pull_two_grid"] = variant(lbm, stream, lbm.LBM_F64, lbm.LBM_PULL_TWO_GRID, vs, nf, peak)
+        variants["f64_double_float_aa"] = variant(lbm, stream, lbm.LBM_F64_DOUBLE_FLOAT, lbm.LBM_AA_INPLACE, vs, nf,
+                                                  peak)
+        variants["f64_double_float_pull"] = variant(lbm, stream, lbm.LBM_F64_DOUBLE_FLOAT, lbm.LBM_PULL_TWO_GRID, vs,
+                                                    nf, peak)
         variants["f32_shifted_aa"] = variant(lbm, stream, lbm.LBM_F32_SHIFTED, lbm.LBM_AA_INPLACE, vs, nf, peak)
         variants["f16_shifted_aa"] = variant(lbm, stream, lbm.LBM_F16_SHIFTED, lbm.LBM_AA_INPLACE, vs, nf, peak)
         c2 = inputs.POROUS_256
@@ -502,7 +507,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep-only", action="store_true", help="profiling: warm-up and timed steps only")
     ap.add_argument("--dims", type=int, default=0, help="profiling: cubic duct of this size instead of 256")
-    ap.add_argument("--precision", default="f64", choices=["f64", "f32", "f16"], help="profiling (with --sweep-only)")
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32", "f16", "f64df"],
+                    help="profiling (with --sweep-only)")
     ap.add_argument("--prop", default="aa", choices=["aa", "pull"], help="profiling (with --sweep-only)")
     args = ap.parse_args()
     if args.dims:

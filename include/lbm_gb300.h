@@ -67,10 +67,17 @@ typedef enum {
   LBM_ERR_TIMEOUT = 6       /* reserved for bounded device-side waits */
 } lbm_status;
 
-/* PDF storage: FP64 values, or the deviation f_i - w_i from the rest state
- * stored in FP32 / FP16 (round to nearest even) with FP32 collision arithmetic.
- * The paper stores FP64 only (Sec. 2); the shifted formats are additions. */
-typedef enum { LBM_F64 = 0, LBM_F32_SHIFTED = 1, LBM_F16_SHIFTED = 2 } lbm_precision;
+/* PDF storage and collision arithmetic. The paper stores FP64 only (Sec. 2);
+ * the other formats are additions.
+ *   LBM_F64              FP64 values, FP64 collision.
+ *   LBM_F32_SHIFTED      the deviation f_i - w_i from the rest state in FP32
+ *                        (round to nearest even), FP32 collision.
+ *   LBM_F16_SHIFTED      the same deviation in FP16, FP32 collision.
+ *   LBM_F64_DOUBLE_FLOAT FP64 values; the collision runs on f_i - w_i in
+ *                        double-float arithmetic (pairs of FP32, about 48
+ *                        significant bits) and its increment is added to the
+ *                        stored FP64 value. For GPUs whose FP64 units are few. */
+typedef enum { LBM_F64 = 0, LBM_F32_SHIFTED = 1, LBM_F16_SHIFTED = 2, LBM_F64_DOUBLE_FLOAT = 3 } lbm_precision;
 
 /* Full array with flag field (direct) or fluid list + int32 adjacency list
  * with 18 neighbours per node (indirect), Sec. 3 "Lattice Representation". */

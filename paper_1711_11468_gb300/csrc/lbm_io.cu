@@ -284,6 +284,7 @@ unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
     case kF64: { using S = double; __VA_ARGS__; break; }        \
     case kF32: { using S = float; __VA_ARGS__; break; }         \
     case kF16: { using S = __half; __VA_ARGS__; break; }        \
+    case kF64DF: { using S = f64df; __VA_ARGS__; break; }       \
     default: return cudaErrorInvalidValue;                      \
   }
 

@@ -11,6 +11,8 @@
 #include <cuda_fp16.h>
 #include <cstdint>
 
+#include "lbm_df32.cuh"
+
 namespace lbm {
 
 constexpr int Q = 19;
@@ -63,50 +65,6 @@ struct Trt {
   A fk[9];
 };
 
-// ---------------------------------------------------------------- storage
-// FP64 stores f_i; FP32 and FP16 store the deviation d_i = f_i - w_i from the
-// rest state, collided in FP32. The shift keeps the stored magnitudes near the
-// small departures that carry the flow, instead of near w_i.
-template <typename S>
-struct Storage;
-
-template <>
-struct Storage<double> {
-  using A = double;
-  static constexpr bool kShifted = false;
-  __device__ __forceinline__ static double load(const double* p) { return __ldcs(p); }
-  __device__ __forceinline__ static void store(double* p, double v) { __stcs(p, v); }
-  __device__ __forceinline__ static double to_f64(double v, int) { return v; }
-  __device__ __forceinline__ static double from_f64(double f, int) { return f; }
-};
-
-template <>
-struct Storage<float> {
-  using A = float;
-  static constexpr bool kShifted = true;
-  __device__ __forceinline__ static float load(const float* p) { return __ldcs(p); }
-  __device__ __forceinline__ static void store(float* p, float v) { __stcs(p, v); }
-  __device__ __forceinline__ static double to_f64(float v, int i) { return weight(i) + (double)v; }
-  __device__ __forceinline__ static float from_f64(double f, int i) { return __double2float_rn(f - weight(i)); }
-};
-
-template <>
-struct Storage<__half> {
-  using A = float;
-  static constexpr bool kShifted = true;
-  __device__ __forceinline__ static float load(const __half* p) {
-    return __half2float(__ushort_as_half(__ldcs(reinterpret_cast<const unsigned short*>(p))));
-  }
-  __device__ __forceinline__ static void store(__half* p, float v) {
-    __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(__float2half_rn(v)));
-  }
-  __device__ __forceinline__ static double to_f64(__half v, int i) { return weight(i) + (double)__half2float(v); }
-  __device__ __forceinline__ static __half from_f64(double f, int i) {
-    // FP64 -> FP16 in one rounding (a detour through FP32 could double-round).
-    return __double2half(f - weight(i));
-  }
-};
-
 // ---------------------------------------------------------------- collision
 // TRT collision plus body force on one node, in place on f[19].
 //   rho = sum f_i, j = sum c_i f_i, u = j / rho,
@@ -121,6 +79,8 @@ struct Storage<__half> {
 // With kShifted, f holds d_i = f_i - w_i: then rho = 1 + sum d_i, j = sum c_i d_i
 // (sum c_i w_i = 0), and e_i - w_i = w_i (drho - 3/2 rho u.u + 3 c.j + 9/2 (c.u)(c.j)),
 // the same pairwise algebra with rho replaced by drho in the constant term.
+// With the increment constants (a - 1/2, b - 1/2, rest - 1) the same code
+// returns f*_i - f_i instead of f*_i.
 template <typename A, bool kShifted>
 __device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
   A s[10], d[10];
@@ -130,15 +90,15 @@ __device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
     d[k] = f[k] - f[k + 9];
   }
   const A rho0 = f[0] + (((s[1] + s[2]) + (s[3] + s[4])) + ((s[5] + s[6]) + (s[7] + s[8])) + s[9]);
-  const A rho = kShifted ? A(1) + rho0 : rho0;
+  const A rho = kShifted ? A(1.0f) + rho0 : rho0;
   const A jx = (d[1] + d[4]) + (d[5] + d[6]) + d[7];
   const A jy = (d[2] + d[4]) - d[5] + (d[8] + d[9]);
   const A jz = (d[3] + d[6]) - d[7] + (d[8] - d[9]);
-  const A inv_rho = A(1) / rho;
+  const A inv_rho = A(1.0f) / rho;
   const A ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
   const A usq = ux * ux + uy * uy + uz * uz;
   // constant part of e+ per unit weight: rho0 - 3/2 rho u.u
-  const A base = rho0 - A(1.5) * (rho * usq);
+  const A base = rho0 - A(1.5f) * (rho * usq);
   const A bw[2] = {p.wp_w[0] * base, p.wp_w[1] * base};   // w+ w_c base
 
   f[0] = p.rest * f[0] + p.wp_w0 * base;
@@ -146,14 +106,95 @@ __device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
     const int c = k <= 3 ? 0 : 1;
-    const A cu = A(cx(k)) * ux + A(cy(k)) * uy + A(cz(k)) * uz;
-    const A cj = A(cx(k)) * jx + A(cy(k)) * jy + A(cz(k)) * jz;
+    const A cu = cdot<A>(k, ux, uy, uz);
+    const A cj = cdot<A>(k, jx, jy, jz);
     const A P = p.c4[c] * (cu * cj) + (p.a * s[k] + bw[c]);
     const A M = p.b * d[k] + (p.c3[c] * cj + p.fk[k - 1]);
     f[k] = P + M;
     f[k + 9] = P - M;
   }
 }
+
+// ---------------------------------------------------------------- storage
+// Each storage format defines the register type of a loaded PDF (Raw), the
+// arithmetic type of the collision (A) and relax(), which turns the 19 loaded
+// values of a node into its 19 post-collision values.
+//   double : f_i in FP64, collided in FP64.
+//   float  : d_i = f_i - w_i in FP32, collided in FP32.
+//   __half : d_i = f_i - w_i in FP16, collided in FP32.
+//   f64df  : f_i in FP64; the collision runs in double-float on the deviations
+//            d_i = f_i - w_i and returns the increments f*_i - f_i, which are
+//            added to the exact stored values in FP64.
+// The shift keeps the collided magnitudes near the small departures that carry
+// the flow instead of near w_i.
+struct f64df {
+  double v;
+};
+
+template <typename S>
+struct Storage;
+
+template <>
+struct Storage<double> {
+  using Raw = double;
+  using A = double;
+  static constexpr bool kShifted = false, kIncrement = false;
+  __device__ __forceinline__ static Raw load(const double* p) { return __ldcs(p); }
+  __device__ __forceinline__ static void store(double* p, Raw v) { __stcs(p, v); }
+  __device__ __forceinline__ static void relax(Raw (&f)[Q], const Trt<A>& p) { collide<A, false>(f, p); }
+  __device__ __forceinline__ static double to_f64(double v, int) { return v; }
+  __device__ __forceinline__ static double from_f64(double f, int) { return f; }
+};
+
+template <>
+struct Storage<float> {
+  using Raw = float;
+  using A = float;
+  static constexpr bool kShifted = true, kIncrement = false;
+  __device__ __forceinline__ static Raw load(const float* p) { return __ldcs(p); }
+  __device__ __forceinline__ static void store(float* p, Raw v) { __stcs(p, v); }
+  __device__ __forceinline__ static void relax(Raw (&f)[Q], const Trt<A>& p) { collide<A, true>(f, p); }
+  __device__ __forceinline__ static double to_f64(float v, int i) { return weight(i) + (double)v; }
+  __device__ __forceinline__ static float from_f64(double f, int i) { return __double2float_rn(f - weight(i)); }
+};
+
+template <>
+struct Storage<__half> {
+  using Raw = float;
+  using A = float;
+  static constexpr bool kShifted = true, kIncrement = false;
+  __device__ __forceinline__ static Raw load(const __half* p) {
+    return __half2float(__ushort_as_half(__ldcs(reinterpret_cast<const unsigned short*>(p))));
+  }
+  __device__ __forceinline__ static void store(__half* p, Raw v) {
+    __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(__float2half_rn(v)));
+  }
+  __device__ __forceinline__ static void relax(Raw (&f)[Q], const Trt<A>& p) { collide<A, true>(f, p); }
+  __device__ __forceinline__ static double to_f64(__half v, int i) { return weight(i) + (double)__half2float(v); }
+  __device__ __forceinline__ static __half from_f64(double f, int i) {
+    // FP64 -> FP16 in one rounding (a detour through FP32 could double-round).
+    return __double2half(f - weight(i));
+  }
+};
+
+template <>
+struct Storage<f64df> {
+  using Raw = double;
+  using A = df32;
+  static constexpr bool kShifted = true, kIncrement = true;
+  __device__ __forceinline__ static Raw load(const f64df* p) { return __ldcs(reinterpret_cast<const double*>(p)); }
+  __device__ __forceinline__ static void store(f64df* p, Raw v) { __stcs(reinterpret_cast<double*>(p), v); }
+  __device__ __forceinline__ static void relax(Raw (&f)[Q], const Trt<A>& p) {
+    df32 d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = split_f64(f[i]) - df32(weight(i));
+    collide<A, true>(d, p);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = (f[i] + f32_to_f64(d[i].hi)) + f32_to_f64(d[i].lo);
+  }
+  __device__ __forceinline__ static double to_f64(f64df v, int) { return v.v; }
+  __device__ __forceinline__ static f64df from_f64(double f, int) { return f64df{f}; }
+};
 
 // Equilibrium in FP64, absolute or shifted by w_i (initialisation only).
 __device__ __forceinline__ double equilibrium_f64(int i, double rho, double ux, double uy, double uz,

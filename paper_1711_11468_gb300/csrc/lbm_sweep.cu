@@ -21,11 +21,18 @@ Trt<Arith<S>> trt_as(const TrtParams& p) {
     t.c3[c] = (A)(3.0 * p.omega_m * w[c]);
   }
   for (int k = 0; k < 9; ++k) t.fk[k] = (A)p.fk[k];
+  if (Storage<S>::kIncrement) {
+    // return f*_i - f_i: the rest direction and the pair terms lose the f_i itself
+    t.a = (A)((1.0 - p.omega_p) * 0.5 - 0.5);
+    t.b = (A)((1.0 - p.omega_m) * 0.5 - 0.5);
+    t.rest = (A)(-p.omega_p);
+  }
   return t;
 }
 template Trt<double> trt_as<double>(const TrtParams&);
 template Trt<float> trt_as<float>(const TrtParams&);
 template Trt<float> trt_as<__half>(const TrtParams&);
+template Trt<df32> trt_as<f64df>(const TrtParams&);
 
 namespace {
 
@@ -143,6 +150,7 @@ cudaError_t launch_sweep(const LatticeView& v, SweepKind kind, const void* src, 
     case kF64: return sweep_typed<double>(v, kind, src, dst, p, threads, s);
     case kF32: return sweep_typed<float>(v, kind, src, dst, p, threads, s);
     case kF16: return sweep_typed<__half>(v, kind, src, dst, p, threads, s);
+    case kF64DF: return sweep_typed<f64df>(v, kind, src, dst, p, threads, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -22,6 +22,8 @@ namespace lbm {
 
 template <typename S>
 using Arith = typename Storage<S>::A;
+template <typename S>
+using RawT = typename Storage<S>::Raw;
 
 // Wrapped neighbour offsets of one cell of a full array.
 struct Nbr {
@@ -53,11 +55,11 @@ __device__ __forceinline__ S* dir(S* base, int i, int64_t stride) {
   return base + (int64_t)i * stride;
 }
 
-template <typename A>
-__device__ __forceinline__ void reverse(A (&f)[Q]) {
+template <typename R>
+__device__ __forceinline__ void reverse(R (&f)[Q]) {
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
-    const A t = f[k];
+    const R t = f[k];
     f[k] = f[k + 9];
     f[k + 9] = t;
   }
@@ -68,11 +70,10 @@ template <typename S, bool kHW>
 __device__ __forceinline__ void pull_dense_node(const S* __restrict__ src, S* __restrict__ dst,
                                                 const uint8_t* __restrict__ flags, int x, int y, int z, int n,
                                                 int nx, int ny, int nz, int64_t stride, const Trt<Arith<S>>& p) {
-  using A = Arith<S>;
   const uint8_t fl = flags[n];
   if (fl == kSolidHalfway) return;
   const Nbr nb(x, y, z, nx, ny, nz);
-  A f[Q];
+  RawT<S> f[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int m = n + nb.up(i);
@@ -84,7 +85,7 @@ __device__ __forceinline__ void pull_dense_node(const S* __restrict__ src, S* __
   if (fl == kSolidFullway)
     reverse(f);
   else
-    collide<A, Storage<S>::kShifted>(f, p);
+    Storage<S>::relax(f, p);
 #pragma unroll
   for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + n, f[i]);
 }
@@ -93,11 +94,10 @@ __device__ __forceinline__ void pull_dense_node(const S* __restrict__ src, S* __
 template <typename S>
 __device__ __forceinline__ void aa_even_node(S* __restrict__ pdf, int64_t k, int64_t stride,
                                              const Trt<Arith<S>>& p) {
-  using A = Arith<S>;
-  A f[Q];
+  RawT<S> f[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) f[i] = Storage<S>::load(dir(pdf, i, stride) + k);
-  collide<A, Storage<S>::kShifted>(f, p);
+  Storage<S>::relax(f, p);
 #pragma unroll
   for (int i = 0; i < Q; ++i) Storage<S>::store(dir(pdf, opp(i), stride) + k, f[i]);
 }
@@ -107,9 +107,8 @@ template <typename S, bool kHW>
 __device__ __forceinline__ void aa_odd_dense_node(S* __restrict__ pdf, const uint8_t* __restrict__ flags, int x,
                                                   int y, int z, int n, int nx, int ny, int nz, int64_t stride,
                                                   const Trt<Arith<S>>& p) {
-  using A = Arith<S>;
   const Nbr nb(x, y, z, nx, ny, nz);
-  A f[Q];
+  RawT<S> f[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int m = n + nb.up(i);
@@ -118,7 +117,7 @@ __device__ __forceinline__ void aa_odd_dense_node(S* __restrict__ pdf, const uin
     else
       f[i] = Storage<S>::load(dir(pdf, opp(i), stride) + m);
   }
-  collide<A, Storage<S>::kShifted>(f, p);
+  Storage<S>::relax(f, p);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int m = n + nb.down(i);
@@ -135,15 +134,14 @@ template <typename S>
 __device__ __forceinline__ void pull_list_node(const S* __restrict__ src, S* __restrict__ dst,
                                                const int32_t* __restrict__ adj, int64_t k, int64_t stride,
                                                const Trt<Arith<S>>& p) {
-  using A = Arith<S>;
-  A f[Q];
+  RawT<S> f[Q];
   f[0] = Storage<S>::load(src + k);
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     const int32_t a = __ldg(adj + (int64_t)(i - 1) * stride + k);
     f[i] = a >= 0 ? Storage<S>::load(dir(src, i, stride) + a) : Storage<S>::load(dir(src, opp(i), stride) + k);
   }
-  collide<A, Storage<S>::kShifted>(f, p);
+  Storage<S>::relax(f, p);
 #pragma unroll
   for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + k, f[i]);
 }
@@ -151,17 +149,16 @@ __device__ __forceinline__ void pull_list_node(const S* __restrict__ src, S* __r
 template <typename S>
 __device__ __forceinline__ void aa_odd_list_node(S* __restrict__ pdf, const int32_t* __restrict__ adj, int64_t k,
                                                  int64_t stride, const Trt<Arith<S>>& p) {
-  using A = Arith<S>;
   int32_t a[Q];
   a[0] = (int32_t)k;
 #pragma unroll
   for (int i = 1; i < Q; ++i) a[i] = __ldg(adj + (int64_t)(i - 1) * stride + k);
-  A f[Q];
+  RawT<S> f[Q];
   f[0] = Storage<S>::load(pdf + k);
 #pragma unroll
   for (int i = 1; i < Q; ++i)
     f[i] = a[i] >= 0 ? Storage<S>::load(dir(pdf, opp(i), stride) + a[i]) : Storage<S>::load(dir(pdf, i, stride) + k);
-  collide<A, Storage<S>::kShifted>(f, p);
+  Storage<S>::relax(f, p);
   Storage<S>::store(pdf + k, f[0]);
 #pragma unroll
   for (int i = 1; i < Q; ++i) {

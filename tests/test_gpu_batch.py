@@ -70,12 +70,13 @@ def oracle_run(orc, sp, flags, k, steps):
     return orc.run(sp["dims"], flags, sp["omega"], orc.omega_minus(sp["omega"], LAM), sp["force"], f0, steps)
 
 
+@pytest.mark.parametrize("prec", [0, 3])
 @pytest.mark.parametrize("prop", [0, 1])
 @pytest.mark.parametrize("tuning", [(128, 1, 0), (256, 2, 2), (64, 8, 1), (512, 4, 8)])
-def test_batch_f64_matches_oracle(lbm, orc, prop, tuning):
+def test_batch_f64_matches_oracle(lbm, orc, prec, prop, tuning):
     specs = small_batch()
     for steps in (3, 8):
-        got, flags = run_batch(lbm, specs, lbm.LBM_F64, prop, steps, tuning)
+        got, flags = run_batch(lbm, specs, prec, prop, steps, tuning)
         for k, sp in enumerate(specs):
             if sp["kind"] == "porous":
                 assert np.array_equal(flags[k], orc.voxelize_spheres(sp["dims"], sp["spheres"], 2))
@@ -83,7 +84,7 @@ def test_batch_f64_matches_oracle(lbm, orc, prop, tuning):
             assert np.abs(got[k] - ref).max() <= 1e-12, (k, sp["kind"], steps)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_batch_equals_one_at_a_time_bitwise(lbm, prec):
     specs = small_batch(seed=8, count=7)
     a, _ = run_batch(lbm, specs, prec, 1, 9, (192, 4, 2), batch=True)

@@ -71,17 +71,18 @@ def duct():
     return c, dims, flags, u
 
 
+@pytest.mark.parametrize("prec,tol", [(0, 1e-14), (3, 1e-13)])
 @pytest.mark.parametrize("prop", [1, 0])
 @pytest.mark.parametrize("steps", [2, 3])
-def test_duct256_lightcone(lbm, orc, duct, prop, steps):
+def test_duct256_lightcone(lbm, orc, duct, prec, tol, prop, steps):
     c, dims, flags, u = duct
-    got, _, _ = gpu_full(lbm, dims, 0, 0, prop, steps, c["omega"], c["force"], flags=flags, u=u,
+    got, _, _ = gpu_full(lbm, dims, prec, 0, prop, steps, c["omega"], c["force"], flags=flags, u=u,
                          periodic=(1, 0, 0), autotune=(prop == 1))
     corners = [(0, 0, 0), (255, 1, 1), (17, 254, 254), (128, 1, 200), (3, 128, 254)]
     for cell in sample_cells(dims, 40, 21 + steps, corners):
         n = cell[0] + dims[0] * (cell[1] + dims[1] * cell[2])
         ref = cone_oracle(orc, dims, flags, u, cell, steps, c["omega"], c["force"])
-        assert np.abs(got[:, n] - ref).max() <= 1e-14, cell
+        assert np.abs(got[:, n] - ref).max() <= tol, cell
 
 
 def test_duct256_1000_steps_mass_and_aa_equals_pull(lbm, duct):
@@ -90,10 +91,15 @@ def test_duct256_1000_steps_mass_and_aa_equals_pull(lbm, duct):
                         autotune=True)
     b, _, mb = gpu_full(lbm, dims, 0, 0, 0, 1000, c["omega"], c["force"], flags=flags, u=u, periodic=(1, 0, 0))
     assert np.array_equal(a, b)
+    del b
+    # double-float collision: stays within the FP64 bar of the FP64-arithmetic run over 1000 steps
+    d, _, md = gpu_full(lbm, dims, 3, 0, 1, 1000, c["omega"], c["force"], flags=flags, u=u, periodic=(1, 0, 0),
+                        autotune=True)
+    assert np.abs(d - a).max() <= 1e-12
     N = flags.size
     rho0 = 1.0 * N   # equilibrium at rho = 1 in every cell holding PDFs (walls included)
-    assert abs(ma[0] - rho0) / rho0 <= 1e-13
-    assert abs(mb[0] - rho0) / rho0 <= 1e-13
+    for m in (ma, mb, md):
+        assert abs(m[0] - rho0) / rho0 <= 1e-13
 
 
 @pytest.fixture(scope="module")
@@ -117,11 +123,12 @@ def brute_flags(dims, spheres, cells):
     return np.where(inside, 2, 0).astype(np.uint8)
 
 
+@pytest.mark.parametrize("prec,tol", [(0, 1e-14), (3, 1e-13)])
 @pytest.mark.parametrize("prop", [1, 0])
-def test_porous256_lightcone(lbm, orc, porous, prop):
+def test_porous256_lightcone(lbm, orc, porous, prec, tol, prop):
     c, dims, pack = porous
     steps = 3
-    got, gflags, _ = gpu_full(lbm, dims, 0, 1, prop, steps, c["omega"], c["force"], spheres=pack.spheres)
+    got, gflags, _ = gpu_full(lbm, dims, prec, 1, prop, steps, c["omega"], c["force"], spheres=pack.spheres)
     porosity = float(np.count_nonzero(gflags == 0)) / gflags.size
     assert 0.55 <= porosity <= 0.65, porosity
     u = np.zeros((3, gflags.size))
@@ -132,4 +139,4 @@ def test_porous256_lightcone(lbm, orc, porous, prop):
         assert np.array_equal(gflags[idx], fl)
         n = cell[0] + dims[0] * (cell[1] + dims[1] * cell[2])
         ref = cone_oracle(orc, dims, gflags, u, cell, steps, c["omega"], c["force"])
-        assert np.abs(got[:, n] - ref).max() <= 1e-14, cell
+        assert np.abs(got[:, n] - ref).max() <= tol, cell

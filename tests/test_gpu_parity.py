@@ -1,8 +1,10 @@
 """GPU parity: the CUDA sweep through the C ABI against the FP64 oracle.
 
-FP64 storage must match the oracle to max |df| <= 1e-12 (the FMA-contracted
-device arithmetic differs from the oracle's plain rounding by a few ulp per
-step; 1e-12 leaves three orders of magnitude over what 100 steps accumulate).
+FP64 storage must match the oracle to max |df| <= 1e-12 after 100 steps. The
+FP64-arithmetic sweep (FMA-contracted) differs from the oracle's plain rounding
+by a few ulp per step, so its tests use tighter bounds; the double-float
+collision (about 48 bits, on deviations of size <= 1e-2) adds about 1e-16 per
+step and is held to the 1e-12 bar at 100 steps and 1e-13 on shorter runs.
 Index and geometry work is compared bit for bit.
 """
 import numpy as np
@@ -74,14 +76,18 @@ def random_state(orc, rng, dims, flags):
 
 
 # ---------------------------------------------------- Poiseuille, 64^3, FP64
+F64_PRECS = [0, 3]   # FP64 arithmetic, double-float arithmetic
+
+
+@pytest.mark.parametrize("prec", F64_PRECS)
 @pytest.mark.parametrize("prop", [0, 1])
 @pytest.mark.parametrize("steps", [100, 99])
-def test_poiseuille_64_f64(lbm, orc, prop, steps):
+def test_poiseuille_64_f64(lbm, orc, prec, prop, steps):
     """The paper's verification set-up (Sec. 2.1) on 64^3: walls at y = 0, 63."""
     c = inputs.POISEUILLE_64
     dims = c["dims"]
     fl = inputs.channel_flags(*dims)
-    out = gpu_run(lbm, dims, flags=fl, prop=prop, omega=c["omega"], F=c["force"], steps=steps,
+    out = gpu_run(lbm, dims, flags=fl, prec=prec, prop=prop, omega=c["omega"], F=c["force"], steps=steps,
                   periodic=(1, 0, 1), read="pdfs,moments,profile")
     f0 = orc.init_equilibrium(dims, fl)
     ref = orc.run(dims, fl, c["omega"], orc.omega_minus(c["omega"], c["Lambda"]), c["force"], f0, steps)
@@ -99,10 +105,11 @@ def test_poiseuille_64_f64(lbm, orc, prop, steps):
 CASES = [((37, 11, 9), 32), ((5, 4, 3), 256), ((40, 6, 7), 64), ((2, 3, 2), 32)]
 
 
+@pytest.mark.parametrize("prec", F64_PRECS)
 @pytest.mark.parametrize("dims,threads", CASES)
 @pytest.mark.parametrize("addr", [0, 1])
 @pytest.mark.parametrize("prop", [0, 1])
-def test_random_lattices_f64(lbm, orc, dims, threads, addr, prop):
+def test_random_lattices_f64(lbm, orc, prec, dims, threads, addr, prop):
     rng = np.random.default_rng(abs(hash((dims, addr, prop))) % 2 ** 32)
     fl = random_flags(rng, dims, addr == 1)
     f0 = random_state(orc, rng, dims, fl)
@@ -113,8 +120,8 @@ def test_random_lattices_f64(lbm, orc, dims, threads, addr, prop):
     ref = f0
     done = 0
     for steps in (1, 2, 5):
-        out = gpu_run(lbm, dims, flags=fl, addr=addr, prop=prop, omega=omega, Lam=Lam, F=F, f0=f0, steps=steps,
-                      threads=threads)
+        out = gpu_run(lbm, dims, flags=fl, prec=prec, addr=addr, prop=prop, omega=omega, Lam=Lam, F=F, f0=f0,
+                      steps=steps, threads=threads)
         ref = orc.run(dims, fl, omega, wm, F, ref, steps - done)
         done = steps
         assert np.abs(out["pdfs"] - ref).max() <= 1e-13, (steps, np.abs(out["pdfs"] - ref).max())
@@ -142,26 +149,28 @@ def test_spheres_large_radius_wraps(lbm, orc):
 
 
 # ------------------------------------------------------- state handling
+@pytest.mark.parametrize("prec", F64_PRECS)
 @pytest.mark.parametrize("addr", [0, 1])
 @pytest.mark.parametrize("prop", [0, 1])
-def test_write_read_roundtrip_bitexact(lbm, orc, addr, prop):
+def test_write_read_roundtrip_bitexact(lbm, orc, prec, addr, prop):
     rng = np.random.default_rng(11)
     dims = (13, 9, 7)
     fl = random_flags(rng, dims, addr == 1)
     f0 = random_state(orc, rng, dims, fl)
-    out = gpu_run(lbm, dims, flags=fl, addr=addr, prop=prop, f0=f0, steps=0)
+    out = gpu_run(lbm, dims, flags=fl, prec=prec, addr=addr, prop=prop, f0=f0, steps=0)
     assert np.array_equal(out["pdfs"], f0)
 
 
+@pytest.mark.parametrize("prec", F64_PRECS)
 @pytest.mark.parametrize("addr", [0, 1])
 @pytest.mark.parametrize("prop", [0, 1])
-def test_checkpoint_resume_bitexact(lbm, orc, addr, prop):
+def test_checkpoint_resume_bitexact(lbm, orc, prec, addr, prop):
     import torch
     rng = np.random.default_rng(12)
     dims = (16, 10, 6)
     fl = random_flags(rng, dims, addr == 1)
     f0 = random_state(orc, rng, dims, fl)
-    kw = dict(flags=fl, addr=addr, prop=prop, omega=1.3, F=(1e-5, 0, 0))
+    kw = dict(flags=fl, prec=prec, addr=addr, prop=prop, omega=1.3, F=(1e-5, 0, 0))
     full = gpu_run(lbm, dims, f0=f0, steps=14, **kw)["pdfs"]
     half = gpu_run(lbm, dims, f0=f0, steps=7, **kw)["pdfs"]
     resumed = gpu_run(lbm, dims, f0=half, steps=7, **kw)["pdfs"]
@@ -169,25 +178,28 @@ def test_checkpoint_resume_bitexact(lbm, orc, addr, prop):
     torch.cuda.synchronize()
 
 
-def test_aa_equals_pull_bitwise(lbm, orc):
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_aa_equals_pull_bitwise(lbm, orc, prec):
     rng = np.random.default_rng(13)
     dims = (30, 14, 12)
     fl = random_flags(rng, dims, False)
     f0 = random_state(orc, rng, dims, fl)
     for steps in (2, 6, 17):
-        a = gpu_run(lbm, dims, flags=fl, prop=0, omega=0.9, F=(1e-5, 1e-6, 0), f0=f0, steps=steps)["pdfs"]
-        b = gpu_run(lbm, dims, flags=fl, prop=1, omega=0.9, F=(1e-5, 1e-6, 0), f0=f0, steps=steps)["pdfs"]
+        a = gpu_run(lbm, dims, flags=fl, prec=prec, prop=0, omega=0.9, F=(1e-5, 1e-6, 0), f0=f0, steps=steps)["pdfs"]
+        b = gpu_run(lbm, dims, flags=fl, prec=prec, prop=1, omega=0.9, F=(1e-5, 1e-6, 0), f0=f0, steps=steps)["pdfs"]
         assert np.array_equal(a, b)
 
 
-def test_list_equals_dense_on_periodic_box(lbm, orc):
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_list_equals_dense_on_periodic_box(lbm, orc, prec):
     rng = np.random.default_rng(14)
     dims = (20, 12, 10)
     fl = np.zeros(int(np.prod(dims)), dtype=np.uint8)
     f0 = random_state(orc, rng, dims, fl)
     for prop in (0, 1):
-        a = gpu_run(lbm, dims, flags=fl, addr=0, prop=prop, omega=1.7, F=(0, 1e-5, 0), f0=f0, steps=9)["pdfs"]
-        b = gpu_run(lbm, dims, flags=fl, addr=1, prop=prop, omega=1.7, F=(0, 1e-5, 0), f0=f0, steps=9)["pdfs"]
+        kw = dict(flags=fl, prec=prec, prop=prop, omega=1.7, F=(0, 1e-5, 0), f0=f0, steps=9)
+        a = gpu_run(lbm, dims, addr=0, **kw)["pdfs"]
+        b = gpu_run(lbm, dims, addr=1, **kw)["pdfs"]
         assert np.array_equal(a, b)
 
 
