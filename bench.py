@@ -33,11 +33,13 @@ from paper_1711_11468_gb300 import inputs  # noqa: E402
 WORKLOAD = inputs.DUCT_256
 DIMS = WORKLOAD["dims"]
 # FP64 pipe instructions per fluid lattice update of the FP64 AA sweep, from
-# ncu per-opcode counters (DADD 73, DFMA 57, DMUL 19 per fluid cell; see
-# profiles/dense_aa_f64_duct128_ncu.md), and the
-# FP64 pipe's rate on GB300 (2 per clock per SM at 2.07 GHz).
-FP64_INSTR_PER_FLUP = 149.0
+# ncu per-opcode counters (DADD 69, DFMA 45, DMUL 17 per fluid cell; see
+# profiles/dense_aa_f64_duct128_ncu.md), the FP64 pipe's rate on GB300 (2 per
+# clock per SM at 2.07 GHz), and the DRAM bytes one launch of that sweep moves
+# on the 256^3 duct (dram__bytes_read + write, profiles/dense_aa_duct256_dram_traffic.md).
+FP64_INSTR_PER_FLUP = 131.0
 FP64_INSTR_PER_SEC = 152 * 2 * 2.07e9
+F64_AA_TRAFFIC_PER_LAUNCH = 2.53e9 + 2.45e9
 
 METRIC = "MFLUP/s and % of HBM roofline, FP64 vs FP32/FP16-shifted vs batched, at stated error"
 UNIT = "MFLUP/s"
@@ -144,6 +146,12 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
     t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_mflups(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Replicas: every rank advances its own copy of the workload; the job's
+    throughput is all ranks' fluid updates over the slowest rank's time."""
+    return units_per_rank * world / max_seconds / 1e6
 
 
 def sum_over_ranks(x: float, world: int, device=None) -> float:
@@ -273,6 +281,43 @@ def batch_variant(lbm, stream, steps, peak):
             "roofline_frac_at_152": round(mflups * 1e6 * 152.0 / 1e9 / peak, 4)}
 
 
+def startup_series(y, t, F, nu, a, b, nterms=4001):
+    """Plane Poiseuille start-up from rest: steady parabola minus its decaying modes."""
+    L = b - a
+    s = F / (2 * nu) * (y - a) * (b - y)
+    for n in range(1, nterms, 2):
+        s = s - 4 * F * L * L / (nu * np.pi ** 3 * n ** 3) * np.sin(n * np.pi * (y - a) / L) \
+            * np.exp(-nu * n * n * np.pi ** 2 * t / L ** 2)
+    return s
+
+
+def accuracy_poiseuille64(lbm, stream):
+    """The verification set-up (Sec. 2.1) on 64^3 after 100 steps, per storage
+    format: max-relative error of the mean velocity profile against the analytic
+    start-up series at t + 1/2 and against the FP64-arithmetic GPU sweep."""
+    c = inputs.POISEUILLE_64
+    dims, ny = c["dims"], c["dims"][1]
+    profiles = {}
+    for name, prec in (("f64", lbm.LBM_F64), ("f64_double_float", lbm.LBM_F64_DOUBLE_FLOAT),
+                       ("f32_shifted", lbm.LBM_F32_SHIFTED), ("f16_shifted", lbm.LBM_F16_SHIFTED)):
+        h = lbm.lbm_create_lattice(lbm.make_desc(dims, prec, lbm.LBM_DIRECT, lbm.LBM_AA_INPLACE, (1, 0, 1)), stream)
+        try:
+            lbm.lbm_set_geometry(h, 0, inputs.channel_flags(*dims))
+            lbm.lbm_set_params(h, 0, c["omega"], c["Lambda"], c["force"])
+            lbm.lbm_init_equilibrium(h, 0)
+            lbm.lbm_step(h, c["steps"])
+            profiles[name] = lbm.lbm_read_profile(h, 0, 1, 0)
+        finally:
+            lbm.lbm_destroy(h)
+    nu = (1.0 / c["omega"] - 0.5) / 3.0
+    ana = startup_series(np.arange(ny, dtype=float), c["steps"] + 0.5, c["force"][0], nu, 0.5, ny - 1.5)
+    m = slice(1, ny - 1)
+    ref = profiles["f64"]
+    return {k: {"vs_analytic": float(np.abs(v[m] - ana[m]).max() / np.abs(ana[m]).max()),
+                "vs_f64": float(np.abs(v[m] - ref[m]).max() / np.abs(ref[m]).max())}
+            for k, v in profiles.items()}
+
+
 def microbench(lbm, stream, elem: int = 8, n: int = 1 << 24, reps: int = 5):
     """copy-19 and update-19 (Sec. 4.1) on 19 arrays of n elements: GB/s."""
     import torch
@@ -365,7 +410,7 @@ def run_gpu(args):
     moments = lbm.lbm_read_moments(h, 0)
     lbm.lbm_destroy(h)
 
-    value = nf * args.steps * world / sec_max / 1e6
+    value = whole_job_mflups(nf * args.steps, world, sec_max)
     bpf = bytes_per_flup(8, False, "aa")
     achieved = value / world * 1e6 * bpf / 1e9
 
@@ -384,10 +429,11 @@ def run_gpu(args):
     e2e_sec = time.perf_counter() - t0
     lbm.lbm_destroy(h2)
     e2e_sec = max_over_ranks(e2e_sec, world, f"cuda:{local}")
-    e2e_value = nf * args.steps * world / e2e_sec / 1e6
+    e2e_value = whole_job_mflups(nf * args.steps, world, e2e_sec)
 
     variants = {}
     micro = {}
+    accuracy = {}
     if rank == 0 and not args.no_variants:
         vs = min(args.steps, 200)
         variants["f64_pull_two_grid"] = variant(lbm, stream, lbm.LBM_F64, lbm.LBM_PULL_TWO_GRID, vs, nf, peak)
@@ -407,13 +453,15 @@ def run_gpu(args):
                                                            pack, peak)
         variants["f32_batched_512"] = batch_variant(lbm, stream, min(args.steps, 100), peak)
         micro = microbench(lbm, stream)
+        accuracy = accuracy_poiseuille64(lbm, stream)
 
     # The FP64 sweep is bound by the FP64 pipe (2 FMA per clock per SM on GB300):
     # its ALU roofline counts FP64 pipe instructions per fluid update (ncu).
     fp64_rate = FP64_INSTR_PER_SEC
     alu_achieved = value / world * 1e6 * FP64_INSTR_PER_FLUP
     alu = {"bound": "alu", "achieved": round(alu_achieved / 1e9, 1), "peak": round(fp64_rate / 1e9, 1),
-           "unit": "G FP64 instr/s", "frac": round(alu_achieved / fp64_rate, 4), "traffic": None,
+           "unit": "G FP64 instr/s", "frac": round(alu_achieved / fp64_rate, 4),
+           "traffic": F64_AA_TRAFFIC_PER_LAUNCH, "traffic_per_fluid_cell": round(F64_AA_TRAFFIC_PER_LAUNCH / nf, 1),
            "instr_per_flup": FP64_INSTR_PER_FLUP,
            "peak_source": "152 SMs x 2 FP64 FMA/clock x 2.07 GHz (FMA probe measured 598 G/s)"}
     roofline = alu if alu["frac"] > achieved / peak else {
@@ -444,6 +492,7 @@ def run_gpu(args):
             "clocks": clk,
             "mass_after": moments[0],
             "variants": variants,
+            "accuracy_poiseuille64_max_rel": accuracy,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

@@ -1,0 +1,62 @@
+"""The benchmark's multi-process logic on the CPU: world size 2 over gloo.
+
+On GPUs every rank runs an independent replica of the workload (the sweep has
+no data-path collective); the ranks only meet at barriers around the timed
+region and in the max-over-ranks reduction of the elapsed time."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank), LBM_BENCH_BACKEND="gloo")
+    sys.path.insert(0, ROOT)
+    import bench
+    w, r, _ = bench.dist_setup(world)
+    bench.barrier(w)
+    slowest = bench.max_over_ranks(1.5 + r, w)      # rank r took 1.5 + r seconds
+    total = bench.sum_over_ranks(10.0 * (r + 1), w)
+    value = bench.whole_job_mflups(3.0e6, w, slowest)
+    bench.barrier(w)
+    out.put((r, w, slowest, total, value))
+    import torch.distributed as dist
+    dist.destroy_process_group()
+
+
+def test_two_rank_timing_and_aggregation():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r, w, slowest, total, value in res:
+        assert w == 2
+        assert slowest == 2.5          # the max over ranks, not the local time
+        assert total == 30.0
+        assert value == pytest.approx(3.0e6 * 2 / 2.5 / 1e6)
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2"],
+                       capture_output=True, text=True, env=env, timeout=120)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
