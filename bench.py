@@ -281,6 +281,31 @@ def batch_variant(lbm, stream, steps, peak):
             "roofline_frac_at_152": round(mflups * 1e6 * 152.0 / 1e9 / peak, 4)}
 
 
+def geometry_sweep(lbm, stream, steps):
+    """The paper's heterogeneity study (Sec. 4.5) on 256^3, FP32-shifted AA:
+    `blocks` of edge b with gaps of b (b = 2 ... 16) and the homogeneous `pipe`,
+    each on the full array and on the fluid list (half-way bounce-back)."""
+    out = {}
+    geoms = [(f"blocks_{b}", inputs.blocks_flags(*DIMS, block=b, gap=b), (1, 1, 1)) for b in (2, 4, 8, 16)]
+    geoms.append(("pipe", inputs.pipe_flags(*DIMS, solid=inputs.SOLID_HALFWAY), (1, 0, 0)))
+    for name, flags, per in geoms:
+        nf = int(np.count_nonzero(flags == 0))
+        row = {"porosity": round(nf / flags.size, 4)}
+        for addr, tag in ((lbm.LBM_DIRECT, "full_array"), (lbm.LBM_INDIRECT, "list")):
+            h = lbm.lbm_create_lattice(lbm.make_desc(DIMS, lbm.LBM_F32_SHIFTED, addr, lbm.LBM_AA_INPLACE, per), stream)
+            try:
+                lbm.lbm_set_geometry(h, 0, flags)
+                lbm.lbm_set_params(h, 0, 1.0, 3.0 / 16.0, (1e-6, 0.0, 0.0))
+                lbm.lbm_init_equilibrium(h, 0)
+                lbm.lbm_step(h, 4)
+                sec = time_steps(lbm, h, steps, stream)
+            finally:
+                lbm.lbm_destroy(h)
+            row[tag + "_mflups"] = round(nf * steps / sec / 1e6, 1)
+        out[name] = row
+    return out
+
+
 def startup_series(y, t, F, nu, a, b, nterms=4001):
     """Plane Poiseuille start-up from rest: steady parabola minus its decaying modes."""
     L = b - a
@@ -361,7 +386,7 @@ def variant(lbm, stream, precision, propagation, steps, nf, peak):
 
 
 def run_sweep_only(args):
-    """Profiling mode: build the lattice, then warm-up and timed steps only."""
+    """Profiling mode: build the workload, then warm-up and timed steps only."""
     import torch
 
     from paper_1711_11468_gb300 import lbm
@@ -370,13 +395,39 @@ def run_sweep_only(args):
     stream = torch.cuda.current_stream()
     prec = lbm.PRECISION[args.precision]
     prop = lbm.LBM_AA_INPLACE if args.prop == "aa" else lbm.LBM_PULL_TWO_GRID
-    h, flags = make_duct(lbm, stream, prec, prop)
+    if args.workload == "duct":
+        h, flags = make_duct(lbm, stream, prec, prop)
+        nf = int(np.count_nonzero(flags == 0))
+    elif args.workload == "porous":
+        c = inputs.POROUS_256
+        pack = inputs.sphere_pack(DIMS, c["seed"], c["r_min"], c["r_max"], c["porosity"])
+        desc = lbm.make_desc(DIMS, prec, lbm.LBM_INDIRECT, prop)
+        h = lbm.lbm_create_lattice(desc, stream)
+        lbm.lbm_set_geometry_spheres(h, 0, pack.spheres)
+        lbm.lbm_set_params(h, 0, c["omega"], c["Lambda"], c["force"])
+        lbm.lbm_init_equilibrium(h, 0)
+        nf = lbm.lbm_fluid_count(h, 0)
+    else:
+        specs = inputs.batch_specs(count=args.batch_count, seed=inputs.BATCH_512["seed"])
+        descs = [lbm.make_desc(sp.dims, prec, lbm.LBM_DIRECT if sp.kind == "channel" else lbm.LBM_INDIRECT, prop,
+                               (1, 0, 1) if sp.kind == "channel" else (1, 1, 1)) for sp in specs]
+        h = lbm.lbm_create_batch(descs, stream)
+        for k, sp in enumerate(specs):
+            if sp.kind == "channel":
+                lbm.lbm_set_geometry(h, k, sp.flags)
+            else:
+                lbm.lbm_set_geometry_spheres(h, k, sp.spheres)
+            lbm.lbm_set_params(h, k, sp.omega, sp.Lambda, sp.force)
+            lbm.lbm_init_equilibrium(h, k)
+        nf = sum(lbm.lbm_fluid_count(h, k) for k in range(len(specs)))
+        if args.tuning:
+            lbm.lbm_set_tuning(h, *[int(v) for v in args.tuning.split(",")])
     lbm.lbm_step(h, args.warmup)
     sec = time_steps(lbm, h, args.steps, stream)
-    nf = int(np.count_nonzero(flags == 0))
     lbm.lbm_destroy(h)
-    print(json.dumps({"mode": "sweep-only", "dims": list(DIMS), "precision": args.precision, "prop": args.prop,
-                      "steps": args.steps, "mflups": round(nf * args.steps / sec / 1e6, 1)}), flush=True)
+    print(json.dumps({"mode": "sweep-only", "workload": args.workload, "dims": list(DIMS),
+                      "precision": args.precision, "prop": args.prop, "steps": args.steps,
+                      "mflups": round(nf * args.steps / sec / 1e6, 1)}), flush=True)
 
 
 def run_gpu(args):
@@ -452,6 +503,7 @@ def run_gpu(args):
         variants["f32_list_aa_porous256"] = porous_variant(lbm, stream, lbm.LBM_F32_SHIFTED, lbm.LBM_AA_INPLACE, vs,
                                                            pack, peak)
         variants["f32_batched_512"] = batch_variant(lbm, stream, min(args.steps, 100), peak)
+        variants["f32_aa_geometries256"] = geometry_sweep(lbm, stream, min(args.steps, 50))
         micro = microbench(lbm, stream)
         accuracy = accuracy_poiseuille64(lbm, stream)
 
@@ -559,6 +611,10 @@ def main():
     ap.add_argument("--precision", default="f64", choices=["f64", "f32", "f16", "f64df"],
                     help="profiling (with --sweep-only)")
     ap.add_argument("--prop", default="aa", choices=["aa", "pull"], help="profiling (with --sweep-only)")
+    ap.add_argument("--workload", default="duct", choices=["duct", "porous", "batch"],
+                    help="profiling (with --sweep-only)")
+    ap.add_argument("--batch-count", type=int, default=512, help="profiling: lattices in the batch workload")
+    ap.add_argument("--tuning", default="", help="profiling: threads,cells_per_thread,ctas_per_sm for the batch")
     args = ap.parse_args()
     if args.dims:
         global DIMS

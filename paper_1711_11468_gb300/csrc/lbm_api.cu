@@ -37,6 +37,7 @@ struct Lattice {
   int32_t* adj = nullptr;
   int32_t* cell_of = nullptr;
   int32_t* list_index = nullptr;
+  int* status = nullptr;   // the handle's device status word
   bool has_halfway = false, has_fullway = false;
   bool geometry = false, params = false, init = false;
   double omega = 1.0, Lambda = 0.25;
@@ -58,6 +59,7 @@ struct Lattice {
     v.adj = adj;
     v.cell_of = cell_of;
     v.list_index = list_index;
+    v.status = status;
     return v;
   }
 };
@@ -87,6 +89,7 @@ struct lbm_lattice_s {
   int64_t bytes = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int* d_status = nullptr;   // kernels set bits here (bounded waits that gave up)
 
   void* dalloc(size_t n) {
     if (n == 0) n = 256;
@@ -140,6 +143,18 @@ int cuda_fail(lbm_handle h, cudaError_t e, const char* what) {
     cudaError_t e_ = (expr);                           \
     if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
   } while (0)
+
+// After the stream is drained: did a kernel give up on a bounded wait?
+int check_device_status(lbm_handle h) {
+  int st = 0;
+  cudaError_t e = cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "status word");
+  if (st != 0) {
+    h->poisoned = true;
+    return fail(LBM_ERR_TIMEOUT, "a kernel gave up waiting for an asynchronous copy");
+  }
+  return LBM_OK;
+}
 
 int check_handle(lbm_handle h) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
@@ -220,8 +235,14 @@ int create_impl(const lbm_desc* descs, int32_t count, void* stream, lbm_handle* 
     lbm_destroy(h);
     return fail(LBM_ERR_CUDA, std::string("stream/event creation: ") + cudaGetErrorString(e));
   }
+  h->d_status = static_cast<int*>(h->dalloc(sizeof(int)));
+  if (!h->d_status || cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) {
+    lbm_destroy(h);
+    return fail(LBM_ERR_OOM, "allocation of the status word failed");
+  }
   for (int32_t k = 0; k < count; ++k) {
     Lattice& L = h->lat[k];
+    L.status = h->d_status;
     L.desc = descs[k];
     L.N = (int64_t)L.desc.nx * L.desc.ny * L.desc.nz;
     L.flags = static_cast<uint8_t*>(h->dalloc((size_t)L.N));
@@ -453,6 +474,7 @@ int lbm_destroy(lbm_handle h) {
     free_storage(h, L);
     h->dfree(L.flags, (size_t)L.N);
   }
+  h->dfree(h->d_status, sizeof(int));
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
@@ -553,7 +575,7 @@ int lbm_synchronize(lbm_handle h) {
   if (int rc = check_handle(h)) return rc;
   LBM_CUDA(h, cudaStreamSynchronize(h->stream), "synchronize");
   LBM_CUDA(h, cudaGetLastError(), "asynchronous error");
-  return LBM_OK;
+  return check_device_status(h);
 }
 
 int lbm_steps_done(lbm_handle h, int64_t* steps) {
@@ -581,7 +603,7 @@ int lbm_read_pdfs(lbm_handle h, int32_t lattice, double* out, size_t out_len) {
            "read state");
   LBM_CUDA(h, cudaMemcpyAsync(out, c.p, nb, cudaMemcpyDeviceToHost, h->stream), "copy pdfs");
   LBM_CUDA(h, cudaStreamSynchronize(h->stream), "read sync");
-  return LBM_OK;
+  return check_device_status(h);
 }
 
 int lbm_read_macroscopic(lbm_handle h, int32_t lattice, double* rho, double* u) {
@@ -596,7 +618,7 @@ int lbm_read_macroscopic(lbm_handle h, int32_t lattice, double* rho, double* u) 
   if (rho) LBM_CUDA(h, cudaMemcpyAsync(rho, r.p, nb, cudaMemcpyDeviceToHost, h->stream), "copy rho");
   if (u) LBM_CUDA(h, cudaMemcpyAsync(u, v.p, 3 * nb, cudaMemcpyDeviceToHost, h->stream), "copy u");
   LBM_CUDA(h, cudaStreamSynchronize(h->stream), "macroscopic sync");
-  return LBM_OK;
+  return check_device_status(h);
 }
 
 int lbm_read_profile(lbm_handle h, int32_t lattice, int32_t axis, int32_t comp, double* out, size_t out_len) {
@@ -619,7 +641,7 @@ int lbm_read_profile(lbm_handle h, int32_t lattice, int32_t axis, int32_t comp, 
            "copy");
   LBM_CUDA(h, cudaStreamSynchronize(h->stream), "profile sync");
   for (int p = 0; p < planes; ++p) out[p] = hc[p] ? hs[p] / (double)hc[p] : 0.0;
-  return LBM_OK;
+  return check_device_status(h);
 }
 
 int lbm_read_moments(lbm_handle h, int32_t lattice, double out[4]) {
@@ -636,7 +658,7 @@ int lbm_read_moments(lbm_handle h, int32_t lattice, double out[4]) {
            "moments");
   LBM_CUDA(h, cudaMemcpyAsync(out, d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy moments");
   LBM_CUDA(h, cudaStreamSynchronize(h->stream), "moments sync");
-  return LBM_OK;
+  return check_device_status(h);
 }
 
 int lbm_read_flags(lbm_handle h, int32_t lattice, uint8_t* out, size_t out_len) {

@@ -71,22 +71,25 @@ __device__ __forceinline__ df32 operator/(df32 x, df32 y) {
 
 // FP64 -> double-float. hi takes the leading 24 significant bits (truncated),
 // lo the remaining 29 bits rounded to 24. Exact to 2^-48 relative for
-// |d| in [2^-74, 2^127]; other values (zero, tiny, huge) take the conversion
-// instruction instead.
-__device__ __forceinline__ df32 split_f64(double d) {
+// |d| in [2^-74, 2^127]; `out_of_range` is set for other values (zero, tiny,
+// huge), which the caller converts again with split_f64_slow.
+__device__ __forceinline__ df32 split_f64_fast(double d, bool& out_of_range) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
   const unsigned hw = (unsigned)(bits >> 32), lw = (unsigned)bits;
   const unsigned e = (hw >> 20) & 0x7FFu;
-  if (e < 949u || e > 1150u) {
-    const float h = __double2float_rz(d);
-    return df32(h, __double2float_rn(d - (double)h));
-  }
+  out_of_range |= (e - 949u) > (1150u - 949u);   // unsigned: e < 949 wraps around
   const unsigned sign = hw & 0x80000000u;
   const unsigned mag = (hw & 0x7FFFFFFFu) - (896u << 20);   // rebias the exponent to FP32
   const unsigned hb = __funnelshift_l(lw, mag, 3) | sign;   // exponent, 23 leading mantissa bits
   const unsigned rem = lw & 0x1FFFFFFFu;                    // the 29 bits hi dropped
   const unsigned scale = sign | ((e - 948u) << 23);         // +-2^(e - 1075)
   return df32(__uint_as_float(hb), __fmul_rn(__uint2float_rn(rem), __uint_as_float(scale)));
+}
+
+// Any FP64 value, through the conversion instructions (FP64 pipe).
+__device__ __forceinline__ df32 split_f64_slow(double d) {
+  const float h = __double2float_rz(d);
+  return df32(h, __double2float_rn(d - (double)h));
 }
 
 // FP32 -> FP64 exactly (normal numbers and zero; FP32 subnormals, below

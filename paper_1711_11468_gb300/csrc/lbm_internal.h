@@ -40,6 +40,7 @@ struct LatticeView {
   const int32_t* adj = nullptr;       // [18][stride], indirect only
   const int32_t* cell_of = nullptr;   // [Nf], indirect only
   const int32_t* list_index = nullptr;  // [N] node of each cell or -1, indirect only
+  int* status = nullptr;                // device status word of the handle (timeouts)
 };
 
 struct TrtParams {

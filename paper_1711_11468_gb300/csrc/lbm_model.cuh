@@ -186,8 +186,13 @@ struct Storage<f64df> {
   __device__ __forceinline__ static void store(f64df* p, Raw v) { __stcs(reinterpret_cast<double*>(p), v); }
   __device__ __forceinline__ static void relax(Raw (&f)[Q], const Trt<A>& p) {
     df32 d[Q];
+    bool out_of_range = false;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = split_f64(f[i]) - df32(weight(i));
+    for (int i = 0; i < Q; ++i) d[i] = split_f64_fast(f[i], out_of_range) - df32(weight(i));
+    if (out_of_range) {   // a zero or extreme PDF somewhere in the node: convert all 19 exactly
+#pragma unroll
+      for (int i = 0; i < Q; ++i) d[i] = split_f64_slow(f[i]) - df32(weight(i));
+    }
     collide<A, true>(d, p);
 #pragma unroll
     for (int i = 0; i < Q; ++i) f[i] = (f[i] + f32_to_f64(d[i].hi)) + f32_to_f64(d[i].lo);

@@ -1,6 +1,9 @@
 // Single-lattice sweep kernels: one thread per cell of the full array (rows of
 // x on a 2-D grid) or per node of the fluid list. The per-node bodies live in
 // lbm_sweep.cuh and are shared with the batched kernel.
+#include <mutex>
+
+#include "lbm_async.cuh"
 #include "lbm_internal.h"
 #include "lbm_sweep.cuh"
 
@@ -97,6 +100,98 @@ __global__ void __launch_bounds__(512) k_list_aa_odd(S* __restrict__ pdf, const 
   aa_odd_list_node<S>(pdf, adj, k, stride, p);
 }
 
+// Fluid-list sweeps with the adjacency staged in shared memory. A persistent
+// grid strides over tiles of T = blockDim.x nodes; while a CTA works on one
+// tile, one elected thread has the next tile's 18 adjacency rows already on
+// their way into the other shared-memory buffer by bulk copy. The gathers then
+// depend on a shared-memory read instead of a global load, and the 18 indices
+// need no registers between the gather and the scatter.
+constexpr int kStagedMaxThreads = 512;
+constexpr size_t staged_smem_bytes(int threads) { return (size_t)2 * 18 * threads * sizeof(int32_t); }
+
+template <typename S, int KIND>
+__global__ void __launch_bounds__(kStagedMaxThreads) k_list_staged(const S* __restrict__ src, S* __restrict__ dst,
+                                                                   const int32_t* __restrict__ adj, int64_t nf,
+                                                                   int64_t stride, Trt<Arith<S>> p, int* status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bar[2];
+  __shared__ int abort_flag;
+  const int T = blockDim.x;
+  const int j = threadIdx.x;
+  int32_t* buf[2] = {reinterpret_cast<int32_t*>(smem), reinterpret_cast<int32_t*>(smem) + 18 * T};
+  const int64_t ntiles = (nf + T - 1) / T;
+  if (j == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    abort_flag = 0;
+  }
+  __syncthreads();
+  // rows of `count` int32 rounded up to 16 bytes: stays inside the padded stride
+  auto issue = [&](int64_t tile, int b) {
+    const int64_t first = tile * T;
+    const int64_t count = nf - first < T ? nf - first : T;
+    const uint32_t row = (uint32_t)((count * 4 + 15) & ~(int64_t)15);
+    mbar_arrive_expect_tx(&bar[b], 18u * row);
+    for (int i = 0; i < 18; ++i) bulk_copy_g2s(buf[b] + i * T, adj + (int64_t)i * stride + first, row, &bar[b]);
+  };
+  uint32_t parity[2] = {0u, 0u};
+  bool pending[2] = {false, false};   // thread 0's view of copies in flight
+  int it = 0;
+  int64_t t = blockIdx.x;
+  if (j == 0 && t < ntiles) {
+    issue(t, 0);
+    pending[0] = true;
+  }
+  for (; t < ntiles; t += gridDim.x, ++it) {
+    const int b = it & 1;
+    const int64_t tn = t + gridDim.x;
+    if (j == 0 && tn < ntiles) {
+      fence_proxy_async_smem();   // the reads of buf[b^1] (previous tile) are ordered before its refill
+      issue(tn, b ^ 1);
+      pending[b ^ 1] = true;
+    }
+    const bool ok = mbar_wait_bounded(&bar[b], parity[b]);
+    if (ok) {
+      parity[b] ^= 1u;
+      if (j == 0) pending[b] = false;
+    }
+    if (!ok) {
+      atomicOr(status, kStatusWaitTimeout);
+      abort_flag = 1;
+    } else {
+      const int64_t k = t * T + j;
+      if (k < nf) {
+        if (KIND == kPull)
+          pull_list_node_staged<S>(src, dst, buf[b], T, j, k, stride, p);
+        else
+          aa_odd_list_node_staged<S>(dst, buf[b], T, j, k, stride, p);
+      }
+    }
+    __syncthreads();
+    if (abort_flag) break;
+  }
+  // never leave a copy in flight into shared memory that is about to be released
+  if (j == 0)
+    for (int b = 0; b < 2; ++b)
+      if (pending[b] && !mbar_wait_bounded(&bar[b], parity[b])) atomicOr(status, kStatusWaitTimeout);
+}
+
+template <typename S, int KIND>
+int staged_grid(int threads, int64_t ntiles) {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_list_staged<S, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)staged_smem_bytes(kStagedMaxThreads));
+  });
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_list_staged<S, KIND>, threads, staged_smem_bytes(threads));
+  const int64_t g = (int64_t)std::max(1, sms) * std::max(1, per_sm);
+  return (int)std::min<int64_t>(g, ntiles);
+}
+
 template <typename S>
 cudaError_t sweep_typed(const LatticeView& v, SweepKind kind, const void* src_, void* dst_, const TrtParams& tp,
                         int threads, cudaStream_t s) {
@@ -127,15 +222,24 @@ cudaError_t sweep_typed(const LatticeView& v, SweepKind kind, const void* src_, 
   } else {
     if (v.n_nodes == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((v.n_nodes + threads - 1) / threads);
+    const int64_t ntiles = blocks;
     switch (kind) {
       case kPull:
-        k_list_pull<S><<<blocks, threads, 0, s>>>(src, dst, v.adj, v.n_nodes, v.stride, p);
+        if (v.status)
+          k_list_staged<S, kPull><<<staged_grid<S, kPull>(threads, ntiles), threads, staged_smem_bytes(threads), s>>>(
+              src, dst, v.adj, v.n_nodes, v.stride, p, v.status);
+        else
+          k_list_pull<S><<<blocks, threads, 0, s>>>(src, dst, v.adj, v.n_nodes, v.stride, p);
         break;
       case kAAEven:
         k_list_aa_even<S><<<blocks, threads, 0, s>>>(dst, v.n_nodes, v.stride, p);
         break;
       case kAAOdd:
-        k_list_aa_odd<S><<<blocks, threads, 0, s>>>(dst, v.adj, v.n_nodes, v.stride, p);
+        if (v.status)
+          k_list_staged<S, kAAOdd><<<staged_grid<S, kAAOdd>(threads, ntiles), threads, staged_smem_bytes(threads),
+                                      s>>>(dst, dst, v.adj, v.n_nodes, v.stride, p, v.status);
+        else
+          k_list_aa_odd<S><<<blocks, threads, 0, s>>>(dst, v.adj, v.n_nodes, v.stride, p);
         break;
     }
   }

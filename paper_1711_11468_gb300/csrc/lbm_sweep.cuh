@@ -170,4 +170,45 @@ __device__ __forceinline__ void aa_odd_list_node(S* __restrict__ pdf, const int3
   }
 }
 
+// The same two list bodies with the node's adjacency in shared memory:
+// sadj[(i-1)*T + j] for direction i of the tile's j-th node.
+template <typename S>
+__device__ __forceinline__ void pull_list_node_staged(const S* __restrict__ src, S* __restrict__ dst,
+                                                      const int32_t* sadj, int T, int j, int64_t k, int64_t stride,
+                                                      const Trt<Arith<S>>& p) {
+  RawT<S> f[Q];
+  f[0] = Storage<S>::load(src + k);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int32_t a = sadj[(i - 1) * T + j];
+    f[i] = a >= 0 ? Storage<S>::load(dir(src, i, stride) + a) : Storage<S>::load(dir(src, opp(i), stride) + k);
+  }
+  Storage<S>::relax(f, p);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + k, f[i]);
+}
+
+template <typename S>
+__device__ __forceinline__ void aa_odd_list_node_staged(S* __restrict__ pdf, const int32_t* sadj, int T, int j,
+                                                        int64_t k, int64_t stride, const Trt<Arith<S>>& p) {
+  RawT<S> f[Q];
+  f[0] = Storage<S>::load(pdf + k);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int32_t a = sadj[(i - 1) * T + j];
+    f[i] = a >= 0 ? Storage<S>::load(dir(pdf, opp(i), stride) + a) : Storage<S>::load(dir(pdf, i, stride) + k);
+  }
+  Storage<S>::relax(f, p);
+  Storage<S>::store(pdf + k, f[0]);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    // re-read from shared memory rather than keep 18 indices live across the collision
+    const int32_t dn = reinterpret_cast<const volatile int32_t*>(sadj)[(opp(i) - 1) * T + j];
+    if (dn >= 0)
+      Storage<S>::store(dir(pdf, i, stride) + dn, f[i]);
+    else
+      Storage<S>::store(dir(pdf, opp(i), stride) + k, f[i]);
+  }
+}
+
 }  // namespace lbm

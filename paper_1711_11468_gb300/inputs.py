@@ -4,8 +4,9 @@ This module serves both the CUDA path and the CPU oracle and holds none of the
 method's arithmetic (no equilibrium, collision, streaming, voxelisation or
 adjacency). It produces only what a user would hand to the library:
 
-  * flag arrays for the paper's ``channel`` geometry (Sec. 2) and its
-    verification slab (Sec. 2.1), and for a duct walled on four sides;
+  * flag arrays for the paper's ``channel``, ``pipe`` and ``blocks``
+    geometries (Sec. 2), its verification slab (Sec. 2.1), and a duct walled
+    on four sides;
   * sphere lists (cx, cy, cz, r) describing a porous medium (the heterogeneous
     case of Sec. 4.5); cells are voxelised by the library and by the oracle,
     each with its own code;
@@ -66,6 +67,30 @@ def duct_flags(nx: int, ny: int, nz: int) -> np.ndarray:
     f[0, :, :] = SOLID_FULLWAY
     f[nz - 1, :, :] = SOLID_FULLWAY
     return f.reshape(-1)
+
+
+def pipe_flags(nx: int, ny: int, nz: int, solid: int = SOLID_FULLWAY) -> np.ndarray:
+    """The paper's `pipe` (Sec. 2): a pipe along x with a staircase circular
+    cross-section. A cell is fluid when its (y, z) centre lies strictly inside
+    the circle of radius min(ny, nz)/2 - 1 about the cross-section's centre,
+    so the boundary layers in y and z are always solid."""
+    cy, cz = (ny - 1) / 2.0, (nz - 1) / 2.0
+    R = min(ny, nz) / 2.0 - 1.0
+    y = np.arange(ny)[:, None]
+    z = np.arange(nz)[None, :]
+    inside = (y - cy) ** 2 + (z - cz) ** 2 < R * R          # [ny, nz]
+    f = np.where(inside.T[:, :, None], FLUID, solid).astype(np.uint8)   # [nz, ny, 1]
+    return np.broadcast_to(f, (nz, ny, nx)).reshape(-1).copy()
+
+
+def blocks_flags(nx: int, ny: int, nz: int, block: int, gap: int, solid: int = SOLID_HALFWAY) -> np.ndarray:
+    """The paper's `blocks` (Sec. 2, Sec. 4.5): cubic obstacles of edge `block`
+    repeated with period block + gap along every axis, starting at gap // 2."""
+    period = block + gap
+    def axis(n):
+        return ((np.arange(n) - gap // 2) % period) < block
+    m = axis(nz)[:, None, None] & axis(ny)[None, :, None] & axis(nx)[None, None, :]
+    return np.where(m, solid, FLUID).astype(np.uint8).reshape(-1)
 
 
 def velocity_perturbation(nx: int, ny: int, nz: int, seed: int, amplitude: float = 0.01,

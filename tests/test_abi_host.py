@@ -121,3 +121,14 @@ def test_channel_and_duct_flags():
     assert np.all(fl[:, 0] == 1) and np.all(fl[:, 4] == 1) and np.all(fl[:, 1:4] == 0)
     fl = inputs.duct_flags(4, 5, 6).reshape(6, 5, 4)
     assert np.all(fl[0] == 1) and np.all(fl[5] == 1) and np.all(fl[1:5, 1:4] == 0)
+
+
+def test_pipe_and_blocks_geometry():
+    fl = inputs.pipe_flags(5, 12, 10).reshape(10, 12, 5)
+    assert np.all(fl[:, 0, :] == 1) and np.all(fl[:, -1, :] == 1) and np.all(fl[0] == 1) and np.all(fl[-1] == 1)
+    assert np.all(fl == fl[:, :, :1])                          # invariant along the pipe axis
+    assert fl[5, 6, 0] == 0 and (fl[:, :, 0] == 0).sum() > 0.5 * 10 * 12 * 0.5
+    assert np.array_equal(fl[:, :, 0], fl[::-1, ::-1, 0])      # symmetric cross-section
+    b = inputs.blocks_flags(16, 16, 16, block=4, gap=4).reshape(16, 16, 16)
+    assert b.sum() // 2 == 8 * 4 ** 3                          # 2 x 2 x 2 blocks of 4^3
+    assert np.all(b[2:6, 2:6, 2:6] == 2) and np.all(b[0:2] == 0)

@@ -262,3 +262,25 @@ def test_error_paths(lbm):
         lbm.lbm_set_geometry(h, 0, inputs.duct_flags(*dims))
     finally:
         lbm.lbm_destroy(h)
+
+
+# ------------------------------------------------ the paper's other geometries
+@pytest.mark.parametrize("geom", ["pipe", "blocks"])
+@pytest.mark.parametrize("addr", [0, 1])
+@pytest.mark.parametrize("prop", [0, 1])
+def test_pipe_and_blocks_f64(lbm, orc, geom, addr, prop):
+    """`pipe` (staircase circular cross-section) and `blocks` (Sec. 2): full-way
+    walls for the full array, half-way for the fluid list."""
+    dims = (20, 18, 14)
+    if geom == "pipe":
+        fl = inputs.pipe_flags(*dims, solid=1 if addr == 0 else 2)
+        periodic = (1, 0, 0)
+    else:
+        fl = inputs.blocks_flags(*dims, block=3, gap=4)
+        periodic = (1, 1, 1)
+    rng = np.random.default_rng(21)
+    f0 = random_state(orc, rng, dims, fl)
+    F = (2e-5, 1e-6, 0.0)
+    out = gpu_run(lbm, dims, flags=fl, addr=addr, prop=prop, omega=1.4, F=F, f0=f0, steps=7, periodic=periodic)
+    ref = orc.run(dims, fl, 1.4, orc.omega_minus(1.4, LAM), F, f0, 7)
+    assert np.abs(out["pdfs"] - ref).max() <= 1e-13
