@@ -76,8 +76,18 @@ typedef enum {
  *   LBM_F64_DOUBLE_FLOAT FP64 values; the collision runs on f_i - w_i in
  *                        double-float arithmetic (pairs of FP32, about 48
  *                        significant bits) and its increment is added to the
- *                        stored FP64 value. For GPUs whose FP64 units are few. */
-typedef enum { LBM_F64 = 0, LBM_F32_SHIFTED = 1, LBM_F16_SHIFTED = 2, LBM_F64_DOUBLE_FLOAT = 3 } lbm_precision;
+ *                        stored FP64 value. For GPUs whose FP64 units are few.
+ *   LBM_F32_SHIFTED_DOUBLE_FLOAT
+ *                        f_i - w_i in FP32, collided in double-float and rounded
+ *                        once when stored: FP32 bytes, with the accuracy that
+ *                        FP32 collision arithmetic loses. */
+typedef enum {
+  LBM_F64 = 0,
+  LBM_F32_SHIFTED = 1,
+  LBM_F16_SHIFTED = 2,
+  LBM_F64_DOUBLE_FLOAT = 3,
+  LBM_F32_SHIFTED_DOUBLE_FLOAT = 4
+} lbm_precision;
 
 /* Full array with flag field (direct) or fluid list + int32 adjacency list
  * with 18 neighbours per node (indirect), Sec. 3 "Lattice Representation". */

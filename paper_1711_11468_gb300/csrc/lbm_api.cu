@@ -173,7 +173,7 @@ int validate_desc(const lbm_desc* d) {
   if (d->nx < 2 || d->ny < 2 || d->nz < 2) return fail(LBM_ERR_ARG, "every dimension must be >= 2");
   const int64_t N = (int64_t)d->nx * d->ny * d->nz;
   if (N >= ((int64_t)1 << 31)) return fail(LBM_ERR_ARG, "lattice too large: N must be < 2^31 cells");
-  if (d->precision < LBM_F64 || d->precision > LBM_F64_DOUBLE_FLOAT) return fail(LBM_ERR_ARG, "bad precision");
+  if (d->precision < LBM_F64 || d->precision > LBM_F32_SHIFTED_DOUBLE_FLOAT) return fail(LBM_ERR_ARG, "bad precision");
   if (d->addressing != LBM_DIRECT && d->addressing != LBM_INDIRECT) return fail(LBM_ERR_ARG, "bad addressing");
   if (d->propagation != LBM_PULL_TWO_GRID && d->propagation != LBM_AA_INPLACE)
     return fail(LBM_ERR_ARG, "bad propagation");

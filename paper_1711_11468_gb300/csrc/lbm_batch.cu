@@ -146,7 +146,7 @@ void fill_typed(void* host_desc, const LatticeView& v, void* pdf_a, void* pdf_b,
 
 size_t batch_lattice_bytes(int prec) {
   return prec == kF64 ? sizeof(BatchDesc<double>)
-                      : (prec == kF64DF ? sizeof(BatchDesc<df32>) : sizeof(BatchDesc<float>));
+                      : ((prec == kF64DF || prec == kF32DF) ? sizeof(BatchDesc<df32>) : sizeof(BatchDesc<float>));
 }
 
 void fill_batch_lattice(int prec, void* host_desc, const LatticeView& v, void* pdf_a, void* pdf_b,
@@ -155,6 +155,7 @@ void fill_batch_lattice(int prec, void* host_desc, const LatticeView& v, void* p
     case kF64: fill_typed<double>(host_desc, v, pdf_a, pdf_b, p); break;
     case kF32: fill_typed<float>(host_desc, v, pdf_a, pdf_b, p); break;
     case kF64DF: fill_typed<f64df>(host_desc, v, pdf_a, pdf_b, p); break;
+    case kF32DF: fill_typed<f32df>(host_desc, v, pdf_a, pdf_b, p); break;
     default: fill_typed<__half>(host_desc, v, pdf_a, pdf_b, p); break;
   }
 }
@@ -169,7 +170,7 @@ int batch_blocks_per_sm(int prec, SweepKind kind, int threads) {
     case kAAOdd: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<S, kAAOdd>, threads, 0); break; \
   }
   if (prec == kF64) { LBM_OCC(double) } else if (prec == kF32) { LBM_OCC(float) }
-  else if (prec == kF64DF) { LBM_OCC(f64df) } else { LBM_OCC(__half) }
+  else if (prec == kF64DF) { LBM_OCC(f64df) } else if (prec == kF32DF) { LBM_OCC(f32df) } else { LBM_OCC(__half) }
 #undef LBM_OCC
   return e == cudaSuccess && n > 0 ? n : 1;
 }
@@ -181,6 +182,7 @@ cudaError_t launch_batch_sweep(int prec, SweepKind kind, const void* d_lattices,
     case kF32: return batch_typed<float>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, s);
     case kF16: return batch_typed<__half>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, s);
     case kF64DF: return batch_typed<f64df>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, s);
+    case kF32DF: return batch_typed<f32df>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -21,11 +21,13 @@ namespace lbm {
 //               half-way link). The AA pattern after an odd number of steps.
 enum Layout : int { kCanonical = 0, kPullForm = 1, kAAForm = 2 };
 
-enum Prec : int { kF64 = 0, kF32 = 1, kF16 = 2, kF64DF = 3 };
+enum Prec : int { kF64 = 0, kF32 = 1, kF16 = 2, kF64DF = 3, kF32DF = 4 };
 
 enum SweepKind : int { kPull = 0, kAAEven = 1, kAAOdd = 2 };
 
-inline int elem_bytes(int prec) { return (prec == kF64 || prec == kF64DF) ? 8 : (prec == kF32 ? 4 : 2); }
+inline int elem_bytes(int prec) {
+  return (prec == kF64 || prec == kF64DF) ? 8 : ((prec == kF32 || prec == kF32DF) ? 4 : 2);
+}
 
 // Everything a kernel needs to address one lattice's storage.
 struct LatticeView {

@@ -125,10 +125,17 @@ __device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
 //   f64df  : f_i in FP64; the collision runs in double-float on the deviations
 //            d_i = f_i - w_i and returns the increments f*_i - f_i, which are
 //            added to the exact stored values in FP64.
+//   f32df  : d_i = f_i - w_i in FP32, collided in double-float and rounded
+//            once on store. FP32 collision arithmetic makes correlated
+//            rounding errors that accumulate over steps; rounding a precisely
+//            collided value only at the store does not.
 // The shift keeps the collided magnitudes near the small departures that carry
 // the flow instead of near w_i.
 struct f64df {
   double v;
+};
+struct f32df {
+  float v;
 };
 
 template <typename S>
@@ -199,6 +206,25 @@ struct Storage<f64df> {
   }
   __device__ __forceinline__ static double to_f64(f64df v, int) { return v.v; }
   __device__ __forceinline__ static f64df from_f64(double f, int) { return f64df{f}; }
+};
+
+template <>
+struct Storage<f32df> {
+  using Raw = float;
+  using A = df32;
+  static constexpr bool kShifted = true, kIncrement = false;
+  __device__ __forceinline__ static Raw load(const f32df* p) { return __ldcs(reinterpret_cast<const float*>(p)); }
+  __device__ __forceinline__ static void store(f32df* p, Raw v) { __stcs(reinterpret_cast<float*>(p), v); }
+  __device__ __forceinline__ static void relax(Raw (&f)[Q], const Trt<A>& p) {
+    df32 d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = df32(f[i]);
+    collide<A, true>(d, p);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = __fadd_rn(d[i].hi, d[i].lo);
+  }
+  __device__ __forceinline__ static double to_f64(f32df v, int i) { return weight(i) + (double)v.v; }
+  __device__ __forceinline__ static f32df from_f64(double f, int i) { return f32df{__double2float_rn(f - weight(i))}; }
 };
 
 // Equilibrium in FP64, absolute or shifted by w_i (initialisation only).

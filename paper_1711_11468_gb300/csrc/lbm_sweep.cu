@@ -36,6 +36,7 @@ template Trt<double> trt_as<double>(const TrtParams&);
 template Trt<float> trt_as<float>(const TrtParams&);
 template Trt<float> trt_as<__half>(const TrtParams&);
 template Trt<df32> trt_as<f64df>(const TrtParams&);
+template Trt<df32> trt_as<f32df>(const TrtParams&);
 
 namespace {
 
@@ -255,6 +256,7 @@ cudaError_t launch_sweep(const LatticeView& v, SweepKind kind, const void* src, 
     case kF32: return sweep_typed<float>(v, kind, src, dst, p, threads, s);
     case kF16: return sweep_typed<__half>(v, kind, src, dst, p, threads, s);
     case kF64DF: return sweep_typed<f64df>(v, kind, src, dst, p, threads, s);
+    case kF32DF: return sweep_typed<f32df>(v, kind, src, dst, p, threads, s);
   }
   return cudaErrorInvalidValue;
 }

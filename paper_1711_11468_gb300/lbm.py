@@ -15,11 +15,12 @@ import os
 import numpy as np
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_STATE, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_UNSUPPORTED, LBM_ERR_TIMEOUT = range(7)
-LBM_F64, LBM_F32_SHIFTED, LBM_F16_SHIFTED, LBM_F64_DOUBLE_FLOAT = 0, 1, 2, 3
+LBM_F64, LBM_F32_SHIFTED, LBM_F16_SHIFTED, LBM_F64_DOUBLE_FLOAT, LBM_F32_SHIFTED_DOUBLE_FLOAT = 0, 1, 2, 3, 4
 LBM_DIRECT, LBM_INDIRECT = 0, 1
 LBM_PULL_TWO_GRID, LBM_AA_INPLACE = 0, 1
 
-PRECISION = {"f64": LBM_F64, "f32": LBM_F32_SHIFTED, "f16": LBM_F16_SHIFTED, "f64df": LBM_F64_DOUBLE_FLOAT}
+PRECISION = {"f64": LBM_F64, "f32": LBM_F32_SHIFTED, "f16": LBM_F16_SHIFTED, "f64df": LBM_F64_DOUBLE_FLOAT,
+             "f32df": LBM_F32_SHIFTED_DOUBLE_FLOAT}
 Q = 19
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblbm_gb300.so")

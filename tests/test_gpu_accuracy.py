@@ -24,7 +24,10 @@ pytestmark = pytest.mark.gpu
 # storage misses the 1e-5 target (about 4e-5: the 1e-8-per-step force increment
 # is rounded against values near 1e-4); FP16 storage stagnates (the increments
 # fall below its resolution), so its bound only asks for a finite result.
-BOUNDS = {0: 1e-9, 3: 1e-9, 1: 1e-4, 2: 1.5}
+# FP32 storage with the double-float collision meets the 1e-5 target: the
+# stored values are rounded once per step, without the correlated rounding of
+# FP32 arithmetic.
+BOUNDS = {0: 1e-9, 3: 1e-9, 1: 1e-4, 2: 1.5, 4: 1e-5}
 
 
 def series(y, t, F, nu, a, b, nterms=4001):
@@ -54,7 +57,7 @@ def reference(orc):
 REPORT = {}
 
 
-@pytest.mark.parametrize("prec", [1, 2, 3, 0])
+@pytest.mark.parametrize("prec", [1, 4, 2, 3, 0])
 def test_channel384_profile_error(lbm, reference, prec):
     import torch
     c = inputs.CHANNEL_384
@@ -81,7 +84,8 @@ def test_channel384_profile_error(lbm, reference, prec):
         "oracle_max_rel_vs_analytic": float(np.abs(ref[m] - ana[m]).max() / np.abs(ana[m]).max()),
         "mass_rel_drift": float(abs(mass - np.prod(dims)) / np.prod(dims)),
     }
-    name = {0: "f64", 1: "f32_shifted", 2: "f16_shifted", 3: "f64_double_float"}[prec]
+    name = {0: "f64", 1: "f32_shifted", 2: "f16_shifted", 3: "f64_double_float",
+            4: "f32_shifted_double_float"}[prec]
     REPORT[name] = err
     path = os.environ.get("LBM_ACCURACY_REPORT")
     if path:

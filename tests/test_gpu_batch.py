@@ -84,7 +84,7 @@ def test_batch_f64_matches_oracle(lbm, orc, prec, prop, tuning):
             assert np.abs(got[k] - ref).max() <= 1e-12, (k, sp["kind"], steps)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 def test_batch_equals_one_at_a_time_bitwise(lbm, prec):
     specs = small_batch(seed=8, count=7)
     a, _ = run_batch(lbm, specs, prec, 1, 9, (192, 4, 2), batch=True)

@@ -178,7 +178,7 @@ def test_checkpoint_resume_bitexact(lbm, orc, prec, addr, prop):
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 def test_aa_equals_pull_bitwise(lbm, orc, prec):
     rng = np.random.default_rng(13)
     dims = (30, 14, 12)
@@ -190,7 +190,7 @@ def test_aa_equals_pull_bitwise(lbm, orc, prec):
         assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 def test_list_equals_dense_on_periodic_box(lbm, orc, prec):
     rng = np.random.default_rng(14)
     dims = (20, 12, 10)
@@ -204,7 +204,7 @@ def test_list_equals_dense_on_periodic_box(lbm, orc, prec):
 
 
 # ------------------------------------------------- reduced-precision storage
-@pytest.mark.parametrize("prec,tol", [(1, 5e-6), (2, 0.1)])
+@pytest.mark.parametrize("prec,tol", [(1, 5e-6), (2, 0.1), (4, 5e-7)])
 def test_shifted_storage_poiseuille_error(lbm, orc, prec, tol):
     """FP32 / FP16 storage of f - w with FP32 arithmetic on the 64^3 channel:
     the mean velocity profile against the FP64 oracle (max-relative)."""
@@ -221,7 +221,7 @@ def test_shifted_storage_poiseuille_error(lbm, orc, prec, tol):
     assert err <= tol, err
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 4])
 def test_shifted_rest_state_exact(lbm, orc, prec):
     """Shifted storage keeps the rest state exactly at zero deviation."""
     dims = (16, 8, 8)
