@@ -223,8 +223,9 @@ int lbm_read_adjacency(lbm_handle h, int32_t lattice, int32_t* out, size_t out_l
 
 /* Kernel launch shape of the handle's sweep. threads: threads per block
  * (multiple of 32 in [32, 512]); cells_per_thread: cells each thread takes per
- * tile of a batch (1, 2, 4 or 8; single lattices use 1), so a tile holds
- * threads*cells_per_thread cells; ctas_per_sm: for a batch, the persistent
+ * tile of a batch (1, 2, 4 or 8), so a tile holds threads*cells_per_thread
+ * cells, or, for a single full-array lattice, 1 or 2 cells of a row per thread
+ * (fluid lists use 1); ctas_per_sm: for a batch, the persistent
  * grid's CTAs per SM (0 = one CTA per tile instead of a persistent grid).
  * lbm_set_tuning fixes the shape (a negative value keeps the current one);
  * lbm_get_tuning returns {threads, cells_per_thread, ctas_per_sm}; lbm_autotune
@@ -241,6 +242,12 @@ int lbm_autotune(lbm_handle h, int32_t steps);
 int lbm_memory_bytes(lbm_handle h, int64_t* bytes);
 
 int lbm_destroy(lbm_handle h);
+
+/* Exercise the bounded-wait path of the staged sweeps on purpose: one CTA arms
+ * an mbarrier for bytes that no copy delivers and gives up after `polls` polls
+ * (1..2^20). Expected result: LBM_ERR_TIMEOUT, with the handle poisoned and the
+ * CUDA context still usable. Nothing faults, traps or hangs. Synchronous. */
+int lbm_selftest_bounded_wait(lbm_handle h, int32_t polls);
 
 /* Thread-local message describing the last failed call ("" if none). */
 const char* lbm_last_error(void);

@@ -397,9 +397,10 @@ cudaError_t issue_step(lbm_handle h, int phase, cudaStream_t s) {
     const LatticeView v = L.view();
     cudaError_t e;
     if (h->prop == LBM_PULL_TWO_GRID)
-      e = launch_sweep(v, kPull, L.pdf[phase], L.pdf[phase ^ 1], L.trt, h->threads, s);
+      e = launch_sweep(v, kPull, L.pdf[phase], L.pdf[phase ^ 1], L.trt, h->threads, h->cells_per_thread, s);
     else
-      e = launch_sweep(v, phase == 0 ? kAAEven : kAAOdd, L.pdf[0], L.pdf[0], L.trt, h->threads, s);
+      e = launch_sweep(v, phase == 0 ? kAAEven : kAAOdd, L.pdf[0], L.pdf[0], L.trt, h->threads, h->cells_per_thread,
+                       s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -700,8 +701,8 @@ int lbm_set_tuning(lbm_handle h, int32_t threads, int32_t cells_per_thread, int3
   if (cells_per_thread >= 0 && cells_per_thread != 1 && cells_per_thread != 2 && cells_per_thread != 4 &&
       cells_per_thread != 8)
     return fail(LBM_ERR_ARG, "cells_per_thread must be 1, 2, 4 or 8");
-  if (cells_per_thread > 1 && !h->batched())
-    return fail(LBM_ERR_UNSUPPORTED, "cells_per_thread > 1 applies to batches only");
+  if (cells_per_thread > 2 && !h->batched())
+    return fail(LBM_ERR_UNSUPPORTED, "a single lattice takes 1 or 2 cells per thread");
   if (ctas_per_sm > 64) return fail(LBM_ERR_ARG, "ctas_per_sm must be <= 64");
   h->drop_graphs();
   if (threads >= 0) h->threads = threads;
@@ -748,7 +749,10 @@ int lbm_autotune(lbm_handle h, int32_t steps) {
       for (int c : {1, 2, 4, 8})
         for (int g : {0, 2, 4, 8}) shapes.push_back({t, c, g});
   } else {
-    for (int t : {64, 128, 192, 256, 384, 512}) shapes.push_back({t, 1, 0});
+    const bool dense = !h->lat[0].indirect();
+    for (int t : {64, 128, 192, 256, 384, 512})
+      for (int c : {1, 2})
+        if (c == 1 || dense) shapes.push_back({t, c, 0});
   }
   Shape best{h->threads, h->cells_per_thread, h->ctas_per_sm};
   float best_ms = 1e30f;
@@ -805,6 +809,14 @@ int lbm_bench_copy19(const void* src, void* dst, int64_t n, int64_t stride_elems
   cudaError_t e = launch_copy19(src, dst, n, stride_elems, elem_bytes, static_cast<cudaStream_t>(cuda_stream));
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("copy-19: ") + cudaGetErrorString(e));
   return LBM_OK;
+}
+
+int lbm_selftest_bounded_wait(lbm_handle h, int32_t polls) {
+  if (int rc = check_handle(h)) return rc;
+  if (polls < 1 || polls > (1 << 20)) return fail(LBM_ERR_ARG, "polls must be in [1, 2^20]");
+  LBM_CUDA(h, launch_wait_selftest((uint32_t)polls, h->d_status, h->stream), "wait self-test");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "wait self-test sync");
+  return check_device_status(h);
 }
 
 int lbm_bench_update19(void* buf, int64_t n, int64_t stride_elems, int32_t elem_bytes, void* cuda_stream) {

@@ -2,6 +2,7 @@
 // arrays concurrently (19 read and 19 write streams), update-19 updates 19
 // arrays in place. They give the "adjusted" roofline bandwidth for the two-grid
 // and the in-place sweeps. Bitwise integer work so any element size is valid.
+#include "lbm_async.cuh"
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -30,6 +31,21 @@ __global__ void __launch_bounds__(256) k_update19(T* __restrict__ buf, int64_t n
   }
 }
 
+// One CTA arms an mbarrier for 16 bytes that no copy will deliver and waits
+// for at most `polls` polls: the bounded-wait path of the staged sweeps, run
+// on purpose. It must give up, set the status bit and return.
+__global__ void k_wait_selftest(uint32_t polls, int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, 16);
+  __syncthreads();
+  if (!mbar_wait_bounded(&bar, 0, polls) && threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
+}
+
 unsigned grid_for(int64_t n) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -49,6 +65,11 @@ cudaError_t launch_copy19(const void* src, void* dst, int64_t n, int64_t stride,
     case 2: k_copy19<unsigned short><<<g, 256, 0, s>>>((const unsigned short*)src, (unsigned short*)dst, n, stride); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(uint32_t polls, int* status, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(polls, status);
   return cudaGetLastError();
 }
 

@@ -52,9 +52,10 @@ struct TrtParams {
 };
 
 // ------------------------------------------------------------ sweep launchers
-// One time step of one lattice. src == dst for the AA kinds.
+// One time step of one lattice. src == dst for the AA kinds. cells_per_thread
+// (1 or 2) applies to full arrays.
 cudaError_t launch_sweep(const LatticeView& v, SweepKind kind, const void* src, void* dst,
-                         const TrtParams& p, int threads, cudaStream_t s);
+                         const TrtParams& p, int threads, int cells_per_thread, cudaStream_t s);
 
 
 // One time step of every lattice of a batch in one launch. d_lattices holds one
@@ -116,5 +117,7 @@ cudaError_t launch_count_flags(const uint8_t* d_flags, int64_t n, unsigned long 
 // ---------------------------------------------------------- micro-benchmarks
 cudaError_t launch_copy19(const void* src, void* dst, int64_t n, int64_t stride, int elem, cudaStream_t s);
 cudaError_t launch_update19(void* buf, int64_t n, int64_t stride, int elem, cudaStream_t s);
+// Bounded-wait self-test: sets the timeout bit of *status after `polls` polls.
+cudaError_t launch_wait_selftest(uint32_t polls, int* status, cudaStream_t s);
 
 }  // namespace lbm

@@ -75,6 +75,83 @@ __global__ void __launch_bounds__(512) k_dense_aa_odd(S* __restrict__ pdf, const
   aa_odd_dense_node<S, kHW>(pdf, flags, x, y, z, n, nx, ny, nz, stride, p);
 }
 
+// Two cells per thread: x and x + blockDim.x of the same row (grid.y covers
+// x-blocks of 2 * blockDim.x).
+template <typename S, bool kHW>
+__global__ void __launch_bounds__(512) k_dense_pull2(const S* __restrict__ src, S* __restrict__ dst,
+                                                     const uint8_t* __restrict__ flags, int nx, int ny, int nz,
+                                                     int64_t stride, Trt<Arith<S>> p) {
+  const int xa = blockIdx.y * 2 * blockDim.x + threadIdx.x, xb = xa + blockDim.x;
+  if (xa >= nx) return;
+  const int row = blockIdx.x;
+  const int z = row / ny, y = row - z * ny;
+  const int na = xa + nx * row, nb_ = xb + nx * row;
+  const bool hb = xb < nx;
+  const uint8_t fa = flags[na], fb = hb ? flags[nb_] : (uint8_t)kSolidHalfway;
+  RawT<S> f[Q], g[Q];
+  if (fa != kSolidHalfway) pull_dense_gather<S, kHW>(src, flags, Nbr(xa, y, z, nx, ny, nz), na, stride, f);
+  if (fb != kSolidHalfway) pull_dense_gather<S, kHW>(src, flags, Nbr(xb, y, z, nx, ny, nz), nb_, stride, g);
+  if (fa != kSolidHalfway) {
+    if (fa == kSolidFullway) reverse(f); else Storage<S>::relax(f, p);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + na, f[i]);
+  }
+  if (fb != kSolidHalfway) {
+    if (fb == kSolidFullway) reverse(g); else Storage<S>::relax(g, p);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + nb_, g[i]);
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(512) k_dense_aa_even2(S* __restrict__ pdf, const uint8_t* __restrict__ flags,
+                                                        int nx, int64_t stride, Trt<Arith<S>> p) {
+  const int xa = blockIdx.y * 2 * blockDim.x + threadIdx.x, xb = xa + blockDim.x;
+  if (xa >= nx) return;
+  const int na = xa + nx * (int)blockIdx.x, nb_ = xb + nx * (int)blockIdx.x;
+  const bool ua = flags[na] == kFluid, ub = xb < nx && flags[nb_] == kFluid;
+  RawT<S> f[Q], g[Q];
+  if (ua)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = Storage<S>::load(dir(pdf, i, stride) + na);
+  if (ub)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = Storage<S>::load(dir(pdf, i, stride) + nb_);
+  if (ua) {
+    Storage<S>::relax(f, p);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Storage<S>::store(dir(pdf, opp(i), stride) + na, f[i]);
+  }
+  if (ub) {
+    Storage<S>::relax(g, p);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Storage<S>::store(dir(pdf, opp(i), stride) + nb_, g[i]);
+  }
+}
+
+template <typename S, bool kHW>
+__global__ void __launch_bounds__(512) k_dense_aa_odd2(S* __restrict__ pdf, const uint8_t* __restrict__ flags,
+                                                       int nx, int ny, int nz, int64_t stride, Trt<Arith<S>> p) {
+  const int xa = blockIdx.y * 2 * blockDim.x + threadIdx.x, xb = xa + blockDim.x;
+  if (xa >= nx) return;
+  const int row = blockIdx.x;
+  const int z = row / ny, y = row - z * ny;
+  const int na = xa + nx * row, nb_ = xb + nx * row;
+  const bool ua = flags[na] == kFluid, ub = xb < nx && flags[nb_] == kFluid;
+  const Nbr ba(xa, y, z, nx, ny, nz), bb(xb < nx ? xb : xa, y, z, nx, ny, nz);
+  RawT<S> f[Q], g[Q];
+  if (ua) aa_odd_dense_gather<S, kHW>(pdf, flags, ba, na, stride, f);
+  if (ub) aa_odd_dense_gather<S, kHW>(pdf, flags, bb, nb_, stride, g);
+  if (ua) {
+    Storage<S>::relax(f, p);
+    aa_odd_dense_scatter<S, kHW>(pdf, flags, ba, na, stride, f);
+  }
+  if (ub) {
+    Storage<S>::relax(g, p);
+    aa_odd_dense_scatter<S, kHW>(pdf, flags, bb, nb_, stride, g);
+  }
+}
+
 // ------------------------------------------------------------ fluid list
 template <typename S>
 __global__ void __launch_bounds__(512) k_list_pull(const S* __restrict__ src, S* __restrict__ dst,
@@ -195,12 +272,32 @@ int staged_grid(int threads, int64_t ntiles) {
 
 template <typename S>
 cudaError_t sweep_typed(const LatticeView& v, SweepKind kind, const void* src_, void* dst_, const TrtParams& tp,
-                        int threads, cudaStream_t s) {
+                        int threads, int cells_per_thread, cudaStream_t s) {
   const S* src = static_cast<const S*>(src_);
   S* dst = static_cast<S*>(dst_);
   const Trt<Arith<S>> p = trt_as<S>(tp);
   if (threads <= 0) threads = 256;
-  if (!v.indirect) {
+  if (!v.indirect && cells_per_thread == 2) {
+    const int bx = std::min(threads, ((v.nx / 2 + 31) / 32) * 32);
+    const dim3 grid((unsigned)(v.ny * v.nz), (unsigned)((v.nx + 2 * bx - 1) / (2 * bx)));
+    switch (kind) {
+      case kPull:
+        if (v.has_halfway)
+          k_dense_pull2<S, true><<<grid, bx, 0, s>>>(src, dst, v.flags, v.nx, v.ny, v.nz, v.stride, p);
+        else
+          k_dense_pull2<S, false><<<grid, bx, 0, s>>>(src, dst, v.flags, v.nx, v.ny, v.nz, v.stride, p);
+        break;
+      case kAAEven:
+        k_dense_aa_even2<S><<<grid, bx, 0, s>>>(dst, v.flags, v.nx, v.stride, p);
+        break;
+      case kAAOdd:
+        if (v.has_halfway)
+          k_dense_aa_odd2<S, true><<<grid, bx, 0, s>>>(dst, v.flags, v.nx, v.ny, v.nz, v.stride, p);
+        else
+          k_dense_aa_odd2<S, false><<<grid, bx, 0, s>>>(dst, v.flags, v.nx, v.ny, v.nz, v.stride, p);
+        break;
+    }
+  } else if (!v.indirect) {
     const int bx = std::min(threads, ((v.nx + 31) / 32) * 32);
     const dim3 grid((unsigned)(v.ny * v.nz), (unsigned)((v.nx + bx - 1) / bx));
     switch (kind) {
@@ -250,13 +347,13 @@ cudaError_t sweep_typed(const LatticeView& v, SweepKind kind, const void* src_, 
 }  // namespace
 
 cudaError_t launch_sweep(const LatticeView& v, SweepKind kind, const void* src, void* dst, const TrtParams& p,
-                         int threads, cudaStream_t s) {
+                         int threads, int cells_per_thread, cudaStream_t s) {
   switch (v.prec) {
-    case kF64: return sweep_typed<double>(v, kind, src, dst, p, threads, s);
-    case kF32: return sweep_typed<float>(v, kind, src, dst, p, threads, s);
-    case kF16: return sweep_typed<__half>(v, kind, src, dst, p, threads, s);
-    case kF64DF: return sweep_typed<f64df>(v, kind, src, dst, p, threads, s);
-    case kF32DF: return sweep_typed<f32df>(v, kind, src, dst, p, threads, s);
+    case kF64: return sweep_typed<double>(v, kind, src, dst, p, threads, cells_per_thread, s);
+    case kF32: return sweep_typed<float>(v, kind, src, dst, p, threads, cells_per_thread, s);
+    case kF16: return sweep_typed<__half>(v, kind, src, dst, p, threads, cells_per_thread, s);
+    case kF64DF: return sweep_typed<f64df>(v, kind, src, dst, p, threads, cells_per_thread, s);
+    case kF32DF: return sweep_typed<f32df>(v, kind, src, dst, p, threads, cells_per_thread, s);
   }
   return cudaErrorInvalidValue;
 }

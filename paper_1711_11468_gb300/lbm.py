@@ -96,6 +96,7 @@ def load(path: str | None = None):
         "lbm_destroy": [H],
         "lbm_bench_copy19": [vp, vp, i64, i64, i32, vp],
         "lbm_bench_update19": [vp, i64, i64, i32, vp],
+        "lbm_selftest_bounded_wait": [H, i32],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -322,6 +323,10 @@ def lbm_destroy(h: Handle):
     if h.ptr:
         _check(load().lbm_destroy(h))
         h.ptr = ctypes.c_void_p()
+
+
+def lbm_selftest_bounded_wait(h: Handle, polls: int = 1000):
+    _check(load().lbm_selftest_bounded_wait(h, int(polls)))
 
 
 def lbm_bench_copy19(src_ptr: int, dst_ptr: int, n: int, stride: int, elem_bytes: int, stream=None):

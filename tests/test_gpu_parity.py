@@ -284,3 +284,82 @@ def test_pipe_and_blocks_f64(lbm, orc, geom, addr, prop):
     out = gpu_run(lbm, dims, flags=fl, addr=addr, prop=prop, omega=1.4, F=F, f0=f0, steps=7, periodic=periodic)
     ref = orc.run(dims, fl, 1.4, orc.omega_minus(1.4, LAM), F, f0, 7)
     assert np.abs(out["pdfs"] - ref).max() <= 1e-13
+
+
+def test_allocator_failure_is_reported(lbm):
+    """An allocator hook that runs dry: the call that needed memory returns
+    LBM_ERR_OOM and the library keeps working once memory is back."""
+    import torch
+    state = {"left": 10 ** 9}
+
+    def alloc(n):
+        if state["left"] <= 0:
+            return 0
+        state["left"] -= 1
+        return torch.cuda.caching_allocator_alloc(n)
+
+    def free(p):
+        torch.cuda.caching_allocator_delete(p)
+
+    lbm.lbm_set_allocator(alloc, free)
+    try:
+        dims = (16, 12, 10)
+        h = lbm.lbm_create_lattice(lbm.make_desc(dims, 0, 0, 1, (1, 0, 1)), torch.cuda.current_stream())
+        try:
+            state["left"] = 0
+            with pytest.raises(lbm.LbmError) as e:
+                lbm.lbm_set_geometry(h, 0, inputs.channel_flags(*dims))
+            assert e.value.code == lbm.LBM_ERR_OOM
+            state["left"] = 10 ** 9
+            lbm.lbm_set_geometry(h, 0, inputs.channel_flags(*dims))
+            lbm.lbm_set_params(h, 0, 1.0, LAM, (1e-5, 0, 0))
+            lbm.lbm_init_equilibrium(h, 0)
+            lbm.lbm_step(h, 3)
+            assert np.isfinite(lbm.lbm_read_moments(h, 0)).all()
+        finally:
+            lbm.lbm_destroy(h)
+    finally:
+        lbm.lbm_set_allocator(None, None)
+
+
+def test_bounded_wait_timeout_is_reported(lbm):
+    """The bounded wait gives up, the host reads LBM_ERR_TIMEOUT, the handle is
+    poisoned, and the context is still usable by a new handle."""
+    import torch
+    s = torch.cuda.current_stream()
+    dims = (8, 8, 8)
+    h = lbm.lbm_create_lattice(lbm.make_desc(dims, 0, 0, 1), s)
+    try:
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_selftest_bounded_wait(h, 1000)
+        assert e.value.code == lbm.LBM_ERR_TIMEOUT
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_step(h, 1)     # poisoned
+    finally:
+        lbm.lbm_destroy(h)
+    out = gpu_run(lbm, dims, flags=np.zeros(512, dtype=np.uint8), omega=1.2, steps=4)
+    assert np.isfinite(out["pdfs"]).all()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("prop", [0, 1])
+def test_two_cells_per_thread_bitwise(lbm, orc, prec, prop):
+    """Two cells of a row per thread changes the schedule, not the arithmetic."""
+    import torch
+    rng = np.random.default_rng(31)
+    dims = (45, 9, 7)                       # odd nx: the last thread of a row has one cell
+    fl = random_flags(rng, dims, False)
+    f0 = random_state(orc, rng, dims, fl)
+    outs = []
+    for cpt, threads in ((1, 64), (2, 32), (2, 64)):
+        h = lbm.lbm_create_lattice(lbm.make_desc(dims, prec, 0, prop), torch.cuda.current_stream())
+        try:
+            lbm.lbm_set_geometry(h, 0, fl)
+            lbm.lbm_set_params(h, 0, 1.3, LAM, (1e-5, -1e-6, 0))
+            lbm.lbm_write_pdfs(h, 0, f0)
+            lbm.lbm_set_tuning(h, threads, cpt)
+            lbm.lbm_step(h, 7)
+            outs.append(lbm.lbm_read_pdfs(h, 0))
+        finally:
+            lbm.lbm_destroy(h)
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
