@@ -217,8 +217,9 @@ int lbm_fluid_count(lbm_handle h, int32_t lattice, int64_t* n_fluid);
  * entry (i-1)*Nf + k for direction i = 1..18 and list node k: the list index
  * of the upstream node x_k - c_i (wrapped) if fluid, else -1 (a bounce-back
  * link). Nodes are the fluid cells in lexicographic order. Table 1's int32
- * adjacency with 18 neighbours. LBM_ERR_ARG for a directly addressed lattice.
- * Synchronous. */
+ * adjacency with 18 neighbours; the device keeps it as 32-bit element offsets
+ * with the bounce-back target already resolved, and this call decodes them.
+ * LBM_ERR_ARG for a directly addressed lattice. Synchronous. */
 int lbm_read_adjacency(lbm_handle h, int32_t lattice, int32_t* out, size_t out_len);
 
 /* Kernel launch shape of the handle's sweep. threads: threads per block

@@ -34,7 +34,7 @@ struct Lattice {
   int64_t N = 0, nf = 0, nstore = 0, stride = 0;
   uint8_t* flags = nullptr;
   void* pdf[2] = {nullptr, nullptr};
-  int32_t* adj = nullptr;
+  uint32_t* link = nullptr;   // [18][stride] element offsets (see LatticeView)
   int32_t* cell_of = nullptr;
   int32_t* list_index = nullptr;
   int* status = nullptr;   // the handle's device status word
@@ -56,7 +56,7 @@ struct Lattice {
     v.indirect = indirect();
     v.has_halfway = has_halfway;
     v.flags = flags;
-    v.adj = adj;
+    v.link = link;
     v.cell_of = cell_of;
     v.list_index = list_index;
     v.status = status;
@@ -261,10 +261,11 @@ void free_storage(lbm_handle h, Lattice& L) {
     h->dfree(p, pb);
     p = nullptr;
   }
-  h->dfree(L.adj, (size_t)18 * L.stride * sizeof(int32_t));
+  h->dfree(L.link, (size_t)18 * L.stride * sizeof(uint32_t));
   h->dfree(L.cell_of, (size_t)L.nf * sizeof(int32_t));
   h->dfree(L.list_index, (size_t)L.N * sizeof(int32_t));
-  L.adj = L.cell_of = L.list_index = nullptr;
+  L.link = nullptr;
+  L.cell_of = L.list_index = nullptr;
 }
 
 // Validate the flags now on the device, build lists and allocate storage.
@@ -302,9 +303,11 @@ int finish_geometry(lbm_handle h, Lattice& L) {
   if (L.indirect()) {
     L.list_index = static_cast<int32_t*>(h->dalloc((size_t)L.N * sizeof(int32_t)));
     L.cell_of = static_cast<int32_t*>(h->dalloc((size_t)L.nf * sizeof(int32_t)));
-    L.adj = static_cast<int32_t*>(h->dalloc((size_t)18 * L.stride * sizeof(int32_t)));
-    if (!L.list_index || !L.cell_of || !L.adj) return fail(LBM_ERR_OOM, "allocation of the adjacency list failed");
-    LBM_CUDA(h, cudaMemsetAsync(L.adj, 0xff, (size_t)18 * L.stride * sizeof(int32_t), h->stream), "memset adj");
+    if ((int64_t)Q * L.stride > (int64_t)UINT32_MAX)
+      return fail(LBM_ERR_UNSUPPORTED, "fluid list too long for 32-bit link offsets (19 * stride >= 2^32)");
+    L.link = static_cast<uint32_t*>(h->dalloc((size_t)18 * L.stride * sizeof(uint32_t)));
+    if (!L.list_index || !L.cell_of || !L.link) return fail(LBM_ERR_OOM, "allocation of the adjacency list failed");
+    LBM_CUDA(h, cudaMemsetAsync(L.link, 0, (size_t)18 * L.stride * sizeof(uint32_t), h->stream), "memset links");
     Scratch tmp(h, (size_t)scan_tmp_elems(L.N) * sizeof(int32_t));
     if (!tmp.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
     Scratch nfbuf(h, sizeof(int64_t));
@@ -313,7 +316,7 @@ int finish_geometry(lbm_handle h, Lattice& L) {
                                h->stream),
              "compaction");
     LatticeView v = L.view();
-    LBM_CUDA(h, launch_adjacency(v, L.list_index, L.adj, h->stream), "adjacency");
+    LBM_CUDA(h, launch_links(v, L.list_index, h->prop == LBM_AA_INPLACE, L.link, h->stream), "adjacency");
     int64_t nf_check = -1;
     LBM_CUDA(h, cudaMemcpyAsync(&nf_check, nfbuf.p, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream), "copy nf");
     LBM_CUDA(h, cudaStreamSynchronize(h->stream), "adjacency sync");
@@ -686,11 +689,25 @@ int lbm_read_adjacency(lbm_handle h, int32_t lattice, int32_t* out, size_t out_l
   if (!L.geometry) return fail(LBM_ERR_STATE, "no geometry set");
   if (!L.indirect()) return fail(LBM_ERR_ARG, "the lattice uses direct addressing: it has no adjacency list");
   if (!out || out_len < (size_t)18 * L.nf) return fail(LBM_ERR_ARG, "output must hold 18*Nf int32");
-  if (L.nf > 0)
-    LBM_CUDA(h, cudaMemcpy2DAsync(out, (size_t)L.nf * sizeof(int32_t), L.adj, (size_t)L.stride * sizeof(int32_t),
-                                  (size_t)L.nf * sizeof(int32_t), 18, cudaMemcpyDeviceToHost, h->stream),
-             "copy adjacency");
+  if (L.nf == 0) return LBM_OK;
+  // the device holds element offsets; decode them back into upstream node indices
+  std::vector<uint32_t> links((size_t)18 * L.nf);
+  LBM_CUDA(h, cudaMemcpy2DAsync(links.data(), (size_t)L.nf * sizeof(uint32_t), L.link,
+                                (size_t)L.stride * sizeof(uint32_t), (size_t)L.nf * sizeof(uint32_t), 18,
+                                cudaMemcpyDeviceToHost, h->stream),
+           "copy adjacency");
   LBM_CUDA(h, cudaStreamSynchronize(h->stream), "adjacency sync");
+  const bool aa = h->prop == LBM_AA_INPLACE;
+  for (int i = 1; i < Q; ++i) {
+    const uint64_t neighbour_slot = (uint64_t)(aa ? opp(i) : i);
+    const uint32_t* src = links.data() + (size_t)(i - 1) * L.nf;
+    int32_t* dst = out + (size_t)(i - 1) * L.nf;
+    for (int64_t k = 0; k < L.nf; ++k) {
+      const uint64_t off = src[k];
+      const uint64_t slot = off / (uint64_t)L.stride;
+      dst[k] = slot == neighbour_slot ? (int32_t)(off - slot * (uint64_t)L.stride) : -1;
+    }
+  }
   return LBM_OK;
 }
 

@@ -19,7 +19,7 @@ template <typename A>
 struct __align__(16) BatchDesc {
   void* pdf[2];            // state grid(s): AA uses pdf[0]; pull alternates
   const uint8_t* flags;    // [N], full array only
-  const int32_t* adj;      // [18][stride], fluid list only
+  const uint32_t* link;    // [18][stride] element offsets, fluid list only
   int64_t stride;
   int nx, ny, nz;
   int indirect, has_halfway, small;   // small: N < 2^24 (fast coordinate split)
@@ -72,12 +72,12 @@ __global__ void __launch_bounds__(512) k_batch(const BatchDesc<Arith<S>>* __rest
       const int64_t node = tile.first + j;
       if (sd.indirect) {
         if (KIND == kPull)
-          pull_list_node<S>(static_cast<const S*>(sd.pdf[phase]), static_cast<S*>(sd.pdf[phase ^ 1]), sd.adj, node,
-                            stride, sd.p);
+          pull_list_node<S>(static_cast<const S*>(sd.pdf[phase]), static_cast<S*>(sd.pdf[phase ^ 1]), sd.link,
+                            node, stride, sd.p);
         else if (KIND == kAAEven)
           aa_even_node<S>(static_cast<S*>(sd.pdf[0]), node, stride, sd.p);
         else
-          aa_odd_list_node<S>(static_cast<S*>(sd.pdf[0]), sd.adj, node, stride, sd.p);
+          aa_odd_list_node<S>(static_cast<S*>(sd.pdf[0]), sd.link, node, stride, sd.p);
       } else {
         const int n = (int)node;
         if (KIND == kAAEven) {
@@ -128,7 +128,7 @@ void fill_typed(void* host_desc, const LatticeView& v, void* pdf_a, void* pdf_b,
   d.pdf[0] = pdf_a;
   d.pdf[1] = pdf_b;
   d.flags = v.flags;
-  d.adj = v.adj;
+  d.link = v.link;
   d.stride = v.stride;
   d.nx = v.nx;
   d.ny = v.ny;

@@ -132,9 +132,13 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(const uint8_t* __restr
   }
 }
 
-// adj[(i-1)*stride + k] = list index of the upstream cell x_k - c_i, or -1.
-__global__ void k_adjacency(int nx, int ny, int nz, int64_t nf, int64_t stride, const int32_t* __restrict__ cell_of,
-                            const int32_t* __restrict__ list_index, int32_t* __restrict__ adj) {
+// For list node k and direction i: the upstream node a = x_k - c_i (wrapped)
+// or -1 if that cell is solid, turned into the element offset the sweep reads
+// f_i from (AA: slot opp(i) of a, or slot i of k; pull: slot i of a, or slot
+// opp(i) of k). The scatter of the AA odd step writes f*_i where f_opp(i) was
+// read, so one table serves both directions.
+__global__ void k_links(int nx, int ny, int nz, int64_t nf, int64_t stride, const int32_t* __restrict__ cell_of,
+                        const int32_t* __restrict__ list_index, bool aa, uint32_t* __restrict__ link) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nf) return;
   const int64_t n = cell_of[k];
@@ -148,7 +152,9 @@ __global__ void k_adjacency(int nx, int ny, int nz, int64_t nf, int64_t stride, 
     ux = ux < 0 ? ux + nx : (ux >= nx ? ux - nx : ux);
     uy = uy < 0 ? uy + ny : (uy >= ny ? uy - ny : uy);
     uz = uz < 0 ? uz + nz : (uz >= nz ? uz - nz : uz);
-    adj[(int64_t)(i - 1) * stride + k] = list_index[(int64_t)ux + (int64_t)nx * ((int64_t)uy + (int64_t)ny * uz)];
+    const int32_t a = list_index[(int64_t)ux + (int64_t)nx * ((int64_t)uy + (int64_t)ny * uz)];
+    const int64_t off = a >= 0 ? (int64_t)(aa ? opp(i) : i) * stride + a : (int64_t)(aa ? i : opp(i)) * stride + k;
+    link[(int64_t)(i - 1) * stride + k] = (uint32_t)off;
   }
 }
 
@@ -201,10 +207,11 @@ cudaError_t launch_compact(const uint8_t* d_flags, int64_t n, int32_t* d_list_in
   return cudaGetLastError();
 }
 
-cudaError_t launch_adjacency(const LatticeView& v, const int32_t* d_list_index, int32_t* d_adj, cudaStream_t s) {
+cudaError_t launch_links(const LatticeView& v, const int32_t* d_list_index, bool aa, uint32_t* d_link,
+                         cudaStream_t s) {
   if (v.n_nodes == 0) return cudaSuccess;
-  k_adjacency<<<(unsigned)((v.n_nodes + 255) / 256), 256, 0, s>>>(v.nx, v.ny, v.nz, v.n_nodes, v.stride, v.cell_of,
-                                                                 d_list_index, d_adj);
+  k_links<<<(unsigned)((v.n_nodes + 255) / 256), 256, 0, s>>>(v.nx, v.ny, v.nz, v.n_nodes, v.stride, v.cell_of,
+                                                             d_list_index, aa, d_link);
   return cudaGetLastError();
 }
 

@@ -39,7 +39,11 @@ struct LatticeView {
   bool indirect = false;
   bool has_halfway = false;
   const uint8_t* flags = nullptr;     // [N]
-  const int32_t* adj = nullptr;       // [18][stride], indirect only
+  // Indirect only: link[(i-1)*stride + k] is the element offset (slot*stride +
+  // node) the sweep reads f_i of node k from, bounce-back already resolved:
+  // AA: slot opp(i) of the upstream node, or slot i of k itself across a
+  // half-way link; pull: slot i of the upstream node, or slot opp(i) of k.
+  const uint32_t* link = nullptr;     // [18][stride]
   const int32_t* cell_of = nullptr;   // [Nf], indirect only
   const int32_t* list_index = nullptr;  // [N] node of each cell or -1, indirect only
   int* status = nullptr;                // device status word of the handle (timeouts)
@@ -106,7 +110,9 @@ cudaError_t launch_voxelize_spheres(int nx, int ny, int nz, const int32_t* d_sph
 int64_t scan_tmp_elems(int64_t n);
 cudaError_t launch_compact(const uint8_t* d_flags, int64_t n, int32_t* d_list_index, int32_t* d_cell_of,
                            int32_t* scan_tmp, int64_t* d_nf, cudaStream_t s);
-cudaError_t launch_adjacency(const LatticeView& v, const int32_t* d_list_index, int32_t* d_adj, cudaStream_t s);
+// The link table of an indirectly addressed lattice for the given propagation.
+cudaError_t launch_links(const LatticeView& v, const int32_t* d_list_index, bool aa, uint32_t* d_link,
+                         cudaStream_t s);
 // Fluid cells on the boundary faces, accumulated into out[6] (zeroed by the
 // caller): out[2a] on the low face of axis a, out[2a+1] on the high face.
 cudaError_t launch_face_fluid(const uint8_t* d_flags, int nx, int ny, int nz, unsigned long long* d_out,

@@ -155,11 +155,11 @@ __global__ void __launch_bounds__(512) k_dense_aa_odd2(S* __restrict__ pdf, cons
 // ------------------------------------------------------------ fluid list
 template <typename S>
 __global__ void __launch_bounds__(512) k_list_pull(const S* __restrict__ src, S* __restrict__ dst,
-                                                   const int32_t* __restrict__ adj, int64_t nf, int64_t stride,
+                                                   const uint32_t* __restrict__ link, int64_t nf, int64_t stride,
                                                    Trt<Arith<S>> p) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nf) return;
-  pull_list_node<S>(src, dst, adj, k, stride, p);
+  pull_list_node<S>(src, dst, link, k, stride, p);
 }
 
 template <typename S>
@@ -171,32 +171,32 @@ __global__ void __launch_bounds__(512) k_list_aa_even(S* __restrict__ pdf, int64
 }
 
 template <typename S>
-__global__ void __launch_bounds__(512) k_list_aa_odd(S* __restrict__ pdf, const int32_t* __restrict__ adj,
+__global__ void __launch_bounds__(512) k_list_aa_odd(S* __restrict__ pdf, const uint32_t* __restrict__ link,
                                                      int64_t nf, int64_t stride, Trt<Arith<S>> p) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nf) return;
-  aa_odd_list_node<S>(pdf, adj, k, stride, p);
+  aa_odd_list_node<S>(pdf, link, k, stride, p);
 }
 
-// Fluid-list sweeps with the adjacency staged in shared memory. A persistent
-// grid strides over tiles of T = blockDim.x nodes; while a CTA works on one
-// tile, one elected thread has the next tile's 18 adjacency rows already on
-// their way into the other shared-memory buffer by bulk copy. The gathers then
-// depend on a shared-memory read instead of a global load, and the 18 indices
-// need no registers between the gather and the scatter.
+// Fluid-list sweeps with the links staged in shared memory. A persistent grid
+// strides over tiles of T = blockDim.x nodes; while a CTA works on one tile,
+// one elected thread has the next tile's 18 link rows already on their way
+// into the other shared-memory buffer by bulk copy. The gathers then depend on
+// a shared-memory read instead of a global load, and the 18 offsets need no
+// registers between the gather and the scatter.
 constexpr int kStagedMaxThreads = 512;
-constexpr size_t staged_smem_bytes(int threads) { return (size_t)2 * 18 * threads * sizeof(int32_t); }
+constexpr size_t staged_smem_bytes(int threads) { return (size_t)2 * 18 * threads * sizeof(uint32_t); }
 
 template <typename S, int KIND>
 __global__ void __launch_bounds__(kStagedMaxThreads) k_list_staged(const S* __restrict__ src, S* __restrict__ dst,
-                                                                   const int32_t* __restrict__ adj, int64_t nf,
+                                                                   const uint32_t* __restrict__ link, int64_t nf,
                                                                    int64_t stride, Trt<Arith<S>> p, int* status) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar[2];
   __shared__ int abort_flag;
   const int T = blockDim.x;
   const int j = threadIdx.x;
-  int32_t* buf[2] = {reinterpret_cast<int32_t*>(smem), reinterpret_cast<int32_t*>(smem) + 18 * T};
+  uint32_t* buf[2] = {reinterpret_cast<uint32_t*>(smem), reinterpret_cast<uint32_t*>(smem) + 18 * T};
   const int64_t ntiles = (nf + T - 1) / T;
   if (j == 0) {
     mbar_init(&bar[0], 1);
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_list_staged(const S* __re
     const int64_t count = nf - first < T ? nf - first : T;
     const uint32_t row = (uint32_t)((count * 4 + 15) & ~(int64_t)15);
     mbar_arrive_expect_tx(&bar[b], 18u * row);
-    for (int i = 0; i < 18; ++i) bulk_copy_g2s(buf[b] + i * T, adj + (int64_t)i * stride + first, row, &bar[b]);
+    for (int i = 0; i < 18; ++i) bulk_copy_g2s(buf[b] + i * T, link + (int64_t)i * stride + first, row, &bar[b]);
   };
   uint32_t parity[2] = {0u, 0u};
   bool pending[2] = {false, false};   // thread 0's view of copies in flight
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_list_staged(const S* __re
         if (KIND == kPull)
           pull_list_node_staged<S>(src, dst, buf[b], T, j, k, stride, p);
         else
-          aa_odd_list_node_staged<S>(dst, buf[b], T, j, k, stride, p);
+          aa_odd_list_node_staged<S>(dst, buf[b], T, j, k, p);
       }
     }
     __syncthreads();
@@ -325,9 +325,9 @@ cudaError_t sweep_typed(const LatticeView& v, SweepKind kind, const void* src_, 
       case kPull:
         if (v.status)
           k_list_staged<S, kPull><<<staged_grid<S, kPull>(threads, ntiles), threads, staged_smem_bytes(threads), s>>>(
-              src, dst, v.adj, v.n_nodes, v.stride, p, v.status);
+              src, dst, v.link, v.n_nodes, v.stride, p, v.status);
         else
-          k_list_pull<S><<<blocks, threads, 0, s>>>(src, dst, v.adj, v.n_nodes, v.stride, p);
+          k_list_pull<S><<<blocks, threads, 0, s>>>(src, dst, v.link, v.n_nodes, v.stride, p);
         break;
       case kAAEven:
         k_list_aa_even<S><<<blocks, threads, 0, s>>>(dst, v.n_nodes, v.stride, p);
@@ -335,9 +335,9 @@ cudaError_t sweep_typed(const LatticeView& v, SweepKind kind, const void* src_, 
       case kAAOdd:
         if (v.status)
           k_list_staged<S, kAAOdd><<<staged_grid<S, kAAOdd>(threads, ntiles), threads, staged_smem_bytes(threads),
-                                      s>>>(dst, dst, v.adj, v.n_nodes, v.stride, p, v.status);
+                                      s>>>(dst, dst, v.link, v.n_nodes, v.stride, p, v.status);
         else
-          k_list_aa_odd<S><<<blocks, threads, 0, s>>>(dst, v.adj, v.n_nodes, v.stride, p);
+          k_list_aa_odd<S><<<blocks, threads, 0, s>>>(dst, v.link, v.n_nodes, v.stride, p);
         break;
     }
   }

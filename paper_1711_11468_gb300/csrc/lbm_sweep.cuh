@@ -174,85 +174,67 @@ __device__ __forceinline__ void aa_odd_dense_scatter(S* __restrict__ pdf, const 
 }
 
 // ------------------------------------------------------------ fluid list
-// adj[(i-1)*stride + k] = list index of the upstream node x_k - c_i, or -1.
+// link[(i-1)*stride + k]: element offset of f_i for node k, bounce-back
+// resolved (see lbm_internal.h). Gathers and scatters are unconditional.
 template <typename S>
 __device__ __forceinline__ void pull_list_node(const S* __restrict__ src, S* __restrict__ dst,
-                                               const int32_t* __restrict__ adj, int64_t k, int64_t stride,
+                                               const uint32_t* __restrict__ link, int64_t k, int64_t stride,
                                                const Trt<Arith<S>>& p) {
   RawT<S> f[Q];
   f[0] = Storage<S>::load(src + k);
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const int32_t a = __ldg(adj + (int64_t)(i - 1) * stride + k);
-    f[i] = a >= 0 ? Storage<S>::load(dir(src, i, stride) + a) : Storage<S>::load(dir(src, opp(i), stride) + k);
-  }
+  for (int i = 1; i < Q; ++i) f[i] = Storage<S>::load(src + __ldg(link + (int64_t)(i - 1) * stride + k));
   Storage<S>::relax(f, p);
 #pragma unroll
   for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + k, f[i]);
 }
 
 template <typename S>
-__device__ __forceinline__ void aa_odd_list_node(S* __restrict__ pdf, const int32_t* __restrict__ adj, int64_t k,
+__device__ __forceinline__ void aa_odd_list_node(S* __restrict__ pdf, const uint32_t* __restrict__ link, int64_t k,
                                                  int64_t stride, const Trt<Arith<S>>& p) {
-  int32_t a[Q];
-  a[0] = (int32_t)k;
+  uint32_t off[Q];
 #pragma unroll
-  for (int i = 1; i < Q; ++i) a[i] = __ldg(adj + (int64_t)(i - 1) * stride + k);
+  for (int i = 1; i < Q; ++i) off[i] = __ldg(link + (int64_t)(i - 1) * stride + k);
   RawT<S> f[Q];
   f[0] = Storage<S>::load(pdf + k);
 #pragma unroll
-  for (int i = 1; i < Q; ++i)
-    f[i] = a[i] >= 0 ? Storage<S>::load(dir(pdf, opp(i), stride) + a[i]) : Storage<S>::load(dir(pdf, i, stride) + k);
+  for (int i = 1; i < Q; ++i) f[i] = Storage<S>::load(pdf + off[i]);
   Storage<S>::relax(f, p);
   Storage<S>::store(pdf + k, f[0]);
+  // f*_i goes where f_opp(i) came from: the downstream node's slot i, or slot opp(i) of k
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const int32_t dn = a[opp(i)];   // downstream node x_k + c_i
-    if (dn >= 0)
-      Storage<S>::store(dir(pdf, i, stride) + dn, f[i]);
-    else
-      Storage<S>::store(dir(pdf, opp(i), stride) + k, f[i]);
-  }
+  for (int i = 1; i < Q; ++i) Storage<S>::store(pdf + off[opp(i)], f[i]);
 }
 
-// The same two list bodies with the node's adjacency in shared memory:
-// sadj[(i-1)*T + j] for direction i of the tile's j-th node.
+// The same two list bodies with the node's links in shared memory:
+// slink[(i-1)*T + j] for direction i of the tile's j-th node.
 template <typename S>
 __device__ __forceinline__ void pull_list_node_staged(const S* __restrict__ src, S* __restrict__ dst,
-                                                      const int32_t* sadj, int T, int j, int64_t k, int64_t stride,
+                                                      const uint32_t* slink, int T, int j, int64_t k, int64_t stride,
                                                       const Trt<Arith<S>>& p) {
   RawT<S> f[Q];
   f[0] = Storage<S>::load(src + k);
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const int32_t a = sadj[(i - 1) * T + j];
-    f[i] = a >= 0 ? Storage<S>::load(dir(src, i, stride) + a) : Storage<S>::load(dir(src, opp(i), stride) + k);
-  }
+  for (int i = 1; i < Q; ++i) f[i] = Storage<S>::load(src + slink[(i - 1) * T + j]);
   Storage<S>::relax(f, p);
 #pragma unroll
   for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + k, f[i]);
 }
 
 template <typename S>
-__device__ __forceinline__ void aa_odd_list_node_staged(S* __restrict__ pdf, const int32_t* sadj, int T, int j,
-                                                        int64_t k, int64_t stride, const Trt<Arith<S>>& p) {
+__device__ __forceinline__ void aa_odd_list_node_staged(S* __restrict__ pdf, const uint32_t* slink, int T, int j,
+                                                        int64_t k, const Trt<Arith<S>>& p) {
   RawT<S> f[Q];
   f[0] = Storage<S>::load(pdf + k);
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const int32_t a = sadj[(i - 1) * T + j];
-    f[i] = a >= 0 ? Storage<S>::load(dir(pdf, opp(i), stride) + a) : Storage<S>::load(dir(pdf, i, stride) + k);
-  }
+  for (int i = 1; i < Q; ++i) f[i] = Storage<S>::load(pdf + slink[(i - 1) * T + j]);
   Storage<S>::relax(f, p);
   Storage<S>::store(pdf + k, f[0]);
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
-    // re-read from shared memory rather than keep 18 indices live across the collision
-    const int32_t dn = reinterpret_cast<const volatile int32_t*>(sadj)[(opp(i) - 1) * T + j];
-    if (dn >= 0)
-      Storage<S>::store(dir(pdf, i, stride) + dn, f[i]);
-    else
-      Storage<S>::store(dir(pdf, opp(i), stride) + k, f[i]);
+    // re-read from shared memory rather than keep 18 offsets live across the collision
+    const uint32_t o = reinterpret_cast<const volatile uint32_t*>(slink)[(opp(i) - 1) * T + j];
+    Storage<S>::store(pdf + o, f[i]);
   }
 }
 
