@@ -422,8 +422,8 @@ def run_sweep_only(args):
             lbm.lbm_set_params(h, k, sp.omega, sp.Lambda, sp.force)
             lbm.lbm_init_equilibrium(h, k)
         nf = sum(lbm.lbm_fluid_count(h, k) for k in range(len(specs)))
-        if args.tuning:
-            lbm.lbm_set_tuning(h, *[int(v) for v in args.tuning.split(",")])
+    if args.tuning:
+        lbm.lbm_set_tuning(h, *[int(v) for v in args.tuning.split(",")])
     lbm.lbm_step(h, args.warmup)
     sec = time_steps(lbm, h, args.steps, stream)
     lbm.lbm_destroy(h)
@@ -618,7 +618,7 @@ def main():
     ap.add_argument("--workload", default="duct", choices=["duct", "porous", "batch"],
                     help="profiling (with --sweep-only)")
     ap.add_argument("--batch-count", type=int, default=512, help="profiling: lattices in the batch workload")
-    ap.add_argument("--tuning", default="", help="profiling: threads,cells_per_thread,ctas_per_sm for the batch")
+    ap.add_argument("--tuning", default="", help="profiling: threads,cells_per_thread,ctas_per_sm")
     args = ap.parse_args()
     if args.dims:
         global DIMS
