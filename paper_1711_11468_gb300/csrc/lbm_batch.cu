@@ -52,6 +52,81 @@ __device__ __forceinline__ void split_cell(int n, int nx, int ny, bool small, fl
   z = zz;
 }
 
+// One node of a tile: the node-local parts shared by both nodes of a pair.
+struct NodeRef {
+  int64_t node;
+  int x, y, z;
+  bool live;   // false: nothing to do (solid cell, or past the end of the tile)
+};
+
+template <typename S, int KIND, typename D>
+__device__ __forceinline__ NodeRef node_ref(const D& sd, int64_t node, bool in_tile) {
+  NodeRef r{node, 0, 0, 0, in_tile};
+  if (!in_tile || sd.indirect) return r;
+  const int n = (int)node;
+  const uint8_t fl = sd.flags[n];
+  // AA: fluid cells only (solids are a no-op). Pull: half-way solids hold nothing;
+  // full-way solids reverse their populations.
+  r.live = KIND == kPull ? fl != kSolidHalfway : fl == kFluid;
+  if (r.live && KIND != kAAEven) split_cell(n, sd.nx, sd.ny, sd.small, sd.inv_nx, sd.inv_ny, r.x, r.y, r.z);
+  return r;
+}
+
+template <typename S, int KIND, typename D>
+__device__ __forceinline__ void gather(const D& sd, int phase, const NodeRef& r, RawT<S> (&f)[Q]) {
+  if (!r.live) return;
+  const int64_t stride = sd.stride;
+  if (KIND == kAAEven) {
+    const S* pdf = static_cast<const S*>(sd.pdf[0]);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = Storage<S>::load(dir(pdf, i, stride) + r.node);
+  } else if (sd.indirect) {
+    list_gather<S>(static_cast<const S*>(sd.pdf[KIND == kPull ? phase : 0]), sd.link, r.node, stride, f);
+  } else {
+    const Nbr nb(r.x, r.y, r.z, sd.nx, sd.ny, sd.nz);
+    const int n = (int)r.node;
+    if (KIND == kPull) {
+      const S* src = static_cast<const S*>(sd.pdf[phase]);
+      if (sd.has_halfway) pull_dense_gather<S, true>(src, sd.flags, nb, n, stride, f);
+      else pull_dense_gather<S, false>(src, sd.flags, nb, n, stride, f);
+    } else {
+      const S* pdf = static_cast<const S*>(sd.pdf[0]);
+      if (sd.has_halfway) aa_odd_dense_gather<S, true>(pdf, sd.flags, nb, n, stride, f);
+      else aa_odd_dense_gather<S, false>(pdf, sd.flags, nb, n, stride, f);
+    }
+  }
+}
+
+template <typename S, int KIND, typename D>
+__device__ __forceinline__ void relax_scatter(const D& sd, int phase, const NodeRef& r, RawT<S> (&f)[Q]) {
+  if (!r.live) return;
+  const int64_t stride = sd.stride;
+  if (KIND == kPull && !sd.indirect && sd.flags[(int)r.node] == kSolidFullway)
+    reverse(f);
+  else
+    Storage<S>::relax(f, sd.p);
+  if (KIND == kAAEven) {
+    S* pdf = static_cast<S*>(sd.pdf[0]);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Storage<S>::store(dir(pdf, opp(i), stride) + r.node, f[i]);
+  } else if (KIND == kPull) {
+    S* dst = static_cast<S*>(sd.pdf[phase ^ 1]);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + r.node, f[i]);
+  } else if (sd.indirect) {
+    list_aa_scatter<S>(static_cast<S*>(sd.pdf[0]), sd.link, r.node, stride, f);
+  } else {
+    const Nbr nb(r.x, r.y, r.z, sd.nx, sd.ny, sd.nz);
+    S* pdf = static_cast<S*>(sd.pdf[0]);
+    if (sd.has_halfway) aa_odd_dense_scatter<S, true>(pdf, sd.flags, nb, (int)r.node, stride, f);
+    else aa_odd_dense_scatter<S, false>(pdf, sd.flags, nb, (int)r.node, stride, f);
+  }
+}
+
+// For 4-byte raw values each thread takes its tile's nodes in pairs (j and
+// j + blockDim.x) and issues both nodes' loads before colliding either: a
+// node's loads cannot otherwise start before the previous node's stores, since
+// both touch the same arrays.
 template <typename S, int KIND>
 __global__ void __launch_bounds__(512) k_batch(const BatchDesc<Arith<S>>* __restrict__ lat,
                                                const BatchTile* __restrict__ tiles, int ntiles, int phase) {
@@ -67,40 +142,22 @@ __global__ void __launch_bounds__(512) k_batch(const BatchDesc<Arith<S>>* __rest
       for (int w = threadIdx.x; w < (int)(sizeof(D) / sizeof(int4)); w += blockDim.x) dst[w] = src[w];
     }
     __syncthreads();
-    const int64_t stride = sd.stride;
-    for (int j = threadIdx.x; j < tile.count; j += blockDim.x) {
-      const int64_t node = tile.first + j;
-      if (sd.indirect) {
-        if (KIND == kPull)
-          pull_list_node<S>(static_cast<const S*>(sd.pdf[phase]), static_cast<S*>(sd.pdf[phase ^ 1]), sd.link,
-                            node, stride, sd.p);
-        else if (KIND == kAAEven)
-          aa_even_node<S>(static_cast<S*>(sd.pdf[0]), node, stride, sd.p);
-        else
-          aa_odd_list_node<S>(static_cast<S*>(sd.pdf[0]), sd.link, node, stride, sd.p);
+    // pairs only where a node's 19 values fit in 19 registers (FP32 and FP16 raw values)
+    constexpr bool kPairs = sizeof(RawT<S>) == 4;
+    for (int j = threadIdx.x; j < tile.count; j += (kPairs ? 2 : 1) * blockDim.x) {
+      const NodeRef ra = node_ref<S, KIND>(sd, tile.first + j, true);
+      RawT<S> f[Q];
+      if constexpr (kPairs) {
+        const int jb = j + blockDim.x;
+        const NodeRef rb = node_ref<S, KIND>(sd, tile.first + jb, jb < tile.count);
+        RawT<S> g[Q];
+        gather<S, KIND>(sd, phase, ra, f);
+        gather<S, KIND>(sd, phase, rb, g);
+        relax_scatter<S, KIND>(sd, phase, ra, f);
+        relax_scatter<S, KIND>(sd, phase, rb, g);
       } else {
-        const int n = (int)node;
-        if (KIND == kAAEven) {
-          if (sd.flags[n] == kFluid) aa_even_node<S>(static_cast<S*>(sd.pdf[0]), n, stride, sd.p);
-          continue;
-        }
-        int x, y, z;
-        split_cell(n, sd.nx, sd.ny, sd.small, sd.inv_nx, sd.inv_ny, x, y, z);
-        if (KIND == kPull) {
-          const S* src = static_cast<const S*>(sd.pdf[phase]);
-          S* dst = static_cast<S*>(sd.pdf[phase ^ 1]);
-          if (sd.has_halfway)
-            pull_dense_node<S, true>(src, dst, sd.flags, x, y, z, n, sd.nx, sd.ny, sd.nz, stride, sd.p);
-          else
-            pull_dense_node<S, false>(src, dst, sd.flags, x, y, z, n, sd.nx, sd.ny, sd.nz, stride, sd.p);
-        } else {
-          if (sd.flags[n] != kFluid) continue;
-          S* pdf = static_cast<S*>(sd.pdf[0]);
-          if (sd.has_halfway)
-            aa_odd_dense_node<S, true>(pdf, sd.flags, x, y, z, n, sd.nx, sd.ny, sd.nz, stride, sd.p);
-          else
-            aa_odd_dense_node<S, false>(pdf, sd.flags, x, y, z, n, sd.nx, sd.ny, sd.nz, stride, sd.p);
-        }
+        gather<S, KIND>(sd, phase, ra, f);
+        relax_scatter<S, KIND>(sd, phase, ra, f);
       }
     }
   }

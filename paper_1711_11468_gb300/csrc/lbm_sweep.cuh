@@ -206,6 +206,24 @@ __device__ __forceinline__ void aa_odd_list_node(S* __restrict__ pdf, const uint
   for (int i = 1; i < Q; ++i) Storage<S>::store(pdf + off[opp(i)], f[i]);
 }
 
+// Gather / scatter halves of the list bodies, for two nodes per thread.
+template <typename S>
+__device__ __forceinline__ void list_gather(const S* __restrict__ pdf, const uint32_t* __restrict__ link, int64_t k,
+                                            int64_t stride, RawT<S> (&f)[Q]) {
+  f[0] = Storage<S>::load(pdf + k);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) f[i] = Storage<S>::load(pdf + __ldg(link + (int64_t)(i - 1) * stride + k));
+}
+
+// AA odd scatter: f*_i where f_opp(i) was gathered (the links are read again, from cache).
+template <typename S>
+__device__ __forceinline__ void list_aa_scatter(S* __restrict__ pdf, const uint32_t* __restrict__ link, int64_t k,
+                                                int64_t stride, const RawT<S> (&f)[Q]) {
+  Storage<S>::store(pdf + k, f[0]);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) Storage<S>::store(pdf + __ldg(link + (int64_t)(opp(i) - 1) * stride + k), f[i]);
+}
+
 // The same two list bodies with the node's links in shared memory:
 // slink[(i-1)*T + j] for direction i of the tile's j-th node.
 template <typename S>
