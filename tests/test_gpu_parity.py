@@ -341,14 +341,19 @@ def test_bounded_wait_timeout_is_reported(lbm):
     assert np.isfinite(out["pdfs"]).all()
 
 
+@pytest.mark.parametrize("halfway", [True, False])
+@pytest.mark.parametrize("nx", [45, 46])     # odd: a lone last cell; even: the vector-access kernels
 @pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("prop", [0, 1])
-def test_two_cells_per_thread_bitwise(lbm, orc, prec, prop):
-    """Two cells of a row per thread changes the schedule, not the arithmetic."""
+def test_two_cells_per_thread_bitwise(lbm, orc, prec, prop, nx, halfway):
+    """Two cells of a row per thread changes the schedule, not the arithmetic
+    (also for pairs with one solid and one fluid cell)."""
     import torch
     rng = np.random.default_rng(31)
-    dims = (45, 9, 7)                       # odd nx: the last thread of a row has one cell
+    dims = (nx, 9, 7)
     fl = random_flags(rng, dims, False)
+    if not halfway:
+        fl[fl == 2] = 1
     f0 = random_state(orc, rng, dims, fl)
     outs = []
     for cpt, threads in ((1, 64), (2, 32), (2, 64)):
