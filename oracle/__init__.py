@@ -20,6 +20,14 @@ Parity status of each function (the pins live in ``tests/test_oracle_*.py``):
   voxelize_spheres          pinned (brute-force numpy voxelisation)
   build_list                pinned (brute-force adjacency, involution, link count)
   macroscopic               pinned (analytic Poiseuille profile)
+  splitmix64 / sr_bits      pinned (published splitmix64 outputs; an independent
+                            numpy splitmix64; the documented bit layout)
+  round_half_stochastic     pinned (FP16 neighbours from numpy, fixed points,
+                            exact mean over all 2^16 draws, odd symmetry,
+                            subnormal spacing, saturation)
+  step_f16_stochastic       pinned (every slot is an FP16 neighbour of the FP64
+                            step's value; seed-averaged mass and momentum match
+                            the FP64 step; full-way reversal is exact)
 """
 from __future__ import annotations
 
@@ -47,7 +55,7 @@ def build(force: bool = False) -> str:
     if force or stale:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fopenmp",
-               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC]
+               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -80,6 +88,16 @@ def _load():
     lib.orc_step.argtypes = [ci, ci, ci, u8p, ctypes.c_double, ctypes.c_double, dp, dp, dp, ci]
     lib.orc_macroscopic.argtypes = [ci, ci, ci, u8p, dp, dp, dp, dp]
     lib.orc_max_threads.restype = ci
+    u64 = ctypes.c_uint64
+    lib.orc_splitmix64.argtypes = [u64, u64]
+    lib.orc_splitmix64.restype = u64
+    lib.orc_sr_bits.argtypes = [u64, u64, u64, ci]
+    lib.orc_sr_bits.restype = ctypes.c_uint32
+    lib.orc_round_half_stochastic.argtypes = [ctypes.c_double, ctypes.c_uint32, dp]
+    lib.orc_round_half_stochastic.restype = ctypes.c_double
+    lib.orc_round_half_stochastic_n.argtypes = [dp, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int64, dp, dp]
+    lib.orc_step_f16_stochastic.argtypes = [ci, ci, ci, u8p, ctypes.c_double, ctypes.c_double, dp, dp, dp,
+                                            u64, u64, i32p, dp]
     _lib = lib
     return lib
 
@@ -218,6 +236,46 @@ def macroscopic(dims, flags, F, f):
     _load().orc_macroscopic(nx, ny, nz, _ptr(flags, ctypes.c_uint8), _ptr(F, ctypes.c_double),
                             _ptr(f, ctypes.c_double), _ptr(rho, ctypes.c_double), _ptr(u, ctypes.c_double))
     return rho, u
+
+
+def splitmix64(seed: int, k: int) -> int:
+    """Output number k (0-based) of splitmix64 seeded `seed`."""
+    return int(_load().orc_splitmix64(seed & (2 ** 64 - 1), k & (2 ** 64 - 1)))
+
+
+def sr_bits(seed: int, t: int, node: int, j: int) -> int:
+    """The 16 random bits of direction j of node `node` at sweep t (FP16 stochastic format)."""
+    return int(_load().orc_sr_bits(seed & (2 ** 64 - 1), t, node, j))
+
+
+def round_half_stochastic(x, r):
+    """Stochastic rounding to FP16 of x with random bits r (arrays broadcast):
+    returns (values as float64, margins in FP16 spacings)."""
+    x, r = np.broadcast_arrays(np.asarray(x, dtype=np.float64), np.asarray(r, dtype=np.uint32))
+    x = np.ascontiguousarray(x)
+    r = np.ascontiguousarray(r)
+    out = np.empty(x.shape)
+    margin = np.empty(x.shape)
+    _load().orc_round_half_stochastic_n(_ptr(x, ctypes.c_double), _ptr(r, ctypes.c_uint32), x.size,
+                                        _ptr(out, ctypes.c_double), _ptr(margin, ctypes.c_double))
+    return out, margin
+
+
+def step_f16_stochastic(dims, flags, omega_plus, omega_minus_, F, d_src, seed: int, t: int, node_of=None):
+    """One push step of the FP16-shifted stochastic format on deviations d = f - w:
+    returns (d(t+1) [19, N], margin [19, N])."""
+    nx, ny, nz = dims
+    flags = _u8(flags)
+    d_src = _f64(d_src)
+    dst = np.zeros_like(d_src)
+    margin = np.empty_like(d_src)
+    F = _f64(F)
+    node_of = None if node_of is None else np.ascontiguousarray(node_of, dtype=np.int32)
+    _load().orc_step_f16_stochastic(nx, ny, nz, _ptr(flags, ctypes.c_uint8), omega_plus, omega_minus_,
+                                    _ptr(F, ctypes.c_double), _ptr(d_src, ctypes.c_double),
+                                    _ptr(dst, ctypes.c_double), seed & (2 ** 64 - 1), t,
+                                    _ptr(node_of, ctypes.c_int32), _ptr(margin, ctypes.c_double))
+    return dst, margin
 
 
 def max_threads() -> int:

@@ -10,6 +10,7 @@
  */
 #include "lbm_oracle.h"
 
+#include <math.h>
 #include <stddef.h>
 #include <stdlib.h>
 #ifdef _OPENMP
@@ -246,6 +247,94 @@ void orc_macroscopic(int nx, int ny, int nz, const uint8_t* flags, const double 
       for (int a = 0; a < 3; ++a) u[(size_t)a * N + n] = r != 0.0 ? (j[a] + 0.5 * F[a]) / r : 0.0;
     }
   }
+}
+
+/* splitmix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014): the state advances by the golden-ratio gamma and
+ * each output is the state passed through the "mix64" finaliser. */
+static uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+uint64_t orc_splitmix64(uint64_t seed, uint64_t k) {
+  return mix64(seed + (k + 1u) * 0x9E3779B97F4A7C15ull);
+}
+
+uint32_t orc_sr_bits(uint64_t seed, uint64_t t, uint64_t node, int j) {
+  uint64_t key = orc_splitmix64(seed, (t << 32) | node);
+  int m = j / 4;
+  uint64_t word = m == 0 ? key : orc_splitmix64(key, (uint64_t)(m - 1));
+  return (uint32_t)((word >> (16 * (j % 4))) & 0xFFFFu);
+}
+
+/* Stochastic rounding to FP16 (see the header). Every step is exact in FP64:
+ * u is a power of two, |x| / u has at most 53 significant bits, and
+ * q + r / 2^16 keeps them (q < 1, r / 2^16 has 16 fraction bits). */
+double orc_round_half_stochastic(double x, uint32_t r, double* margin) {
+  if (isnan(x) || isinf(x)) {
+    if (margin) *margin = INFINITY;
+    return x;
+  }
+  double a = fabs(x);
+  int e;
+  (void)frexp(a, &e);          /* a = m * 2^e with m in [0.5, 1): a in [2^(e-1), 2^e) */
+  int ue = (e - 1) - 10;       /* FP16 spacing for a in [2^(e-1), 2^e) */
+  if (a == 0.0 || ue < -24) ue = -24;
+  double u = ldexp(1.0, ue);
+  double s = a / u;
+  double lo = floor(s);
+  double q = s - lo;
+  double up = q + (double)r / 65536.0;
+  double res;
+  if (q == 0.0) {
+    res = lo * u;
+    if (margin) *margin = INFINITY;
+  } else {
+    res = (up >= 1.0 ? lo + 1.0 : lo) * u;
+    if (margin) *margin = fabs(up - 1.0);
+  }
+  if (res > 65504.0) res = 65504.0;
+  return x < 0 ? -res : res;
+}
+
+void orc_round_half_stochastic_n(const double* x, const uint32_t* r, int64_t n, double* out, double* margin) {
+  for (int64_t k = 0; k < n; ++k) out[k] = orc_round_half_stochastic(x[k], r[k], margin ? &margin[k] : NULL);
+}
+
+void orc_step_f16_stochastic(int nx, int ny, int nz, const uint8_t* flags, double omega_plus,
+                             double omega_minus, const double F[3], const double* d_src, double* d_dst,
+                             uint64_t seed, uint64_t t, const int32_t* node_of, double* margin) {
+  size_t N = (size_t)nx * ny * nz;
+  if (margin)
+    for (size_t k = 0; k < (size_t)ORC_Q * N; ++k) margin[k] = INFINITY;
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        size_t n = (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * (size_t)z);
+        if (flags[n] == 2) continue;
+        double f[ORC_Q], fs[ORC_Q], ds[ORC_Q], mg[ORC_Q];
+        if (flags[n] == 1) {
+          for (int i = 0; i < ORC_Q; ++i) {
+            ds[i] = d_src[(size_t)orc_opposite(i) * N + n];
+            mg[i] = INFINITY;
+          }
+        } else {
+          for (int i = 0; i < ORC_Q; ++i) f[i] = orc_weight(i) + d_src[(size_t)i * N + n];
+          orc_collide_trt(f, omega_plus, omega_minus, F, fs);
+          uint64_t node = node_of ? (uint64_t)node_of[n] : (uint64_t)n;
+          for (int i = 0; i < ORC_Q; ++i)
+            ds[i] = orc_round_half_stochastic(fs[i] - orc_weight(i), orc_sr_bits(seed, t, node, i), &mg[i]);
+        }
+        for (int i = 0; i < ORC_Q; ++i) {
+          int dx = wrap(x + CX[i], nx), dy = wrap(y + CY[i], ny), dz = wrap(z + CZ[i], nz);
+          size_t m = (size_t)dx + (size_t)nx * ((size_t)dy + (size_t)ny * (size_t)dz);
+          size_t slot = flags[m] == 2 ? (size_t)orc_opposite(i) * N + n : (size_t)i * N + m;
+          d_dst[slot] = ds[i];
+          if (margin) margin[slot] = mg[i];
+        }
+      }
 }
 
 int orc_max_threads(void) {

@@ -81,6 +81,54 @@ void orc_step(int nx, int ny, int nz, const uint8_t* flags, double omega_plus,
 void orc_macroscopic(int nx, int ny, int nz, const uint8_t* flags, const double F[3],
                      const double* f, double* rho, double* u);
 
+/* ---------------------------------------------------------------------------
+ * FP16-shifted storage with stochastic rounding (an accuracy remedy for the
+ * FP16-shifted format; not in the paper, whose error study of reduced
+ * precision storage is the verification set-up of Sec. 2.1).
+ *
+ * State: deviations d_i = f_i - w_i, each an FP16 value held in a double.
+ * One step: f = w + d, the FP64 collision and bounce-back of orc_step, then
+ * each post-collision deviation f*_j - w_j of a fluid node is rounded to FP16
+ * stochastically with 16 random bits r(seed, t, node, j); full-way solid
+ * nodes only reverse their (already FP16) values.
+ *
+ * Random bits (counter-based, splitmix64 of Steele, Lea and Flood, OOPSLA
+ * 2014): node `node` at sweep t draws the key
+ *   K = splitmix64 output number ((t << 32) | node) of the stream seeded `seed`,
+ * then the words W_0 = K and W_m = output number m-1 of the stream seeded K
+ * (m = 1..4); direction j takes bits 16*(j mod 4) .. +15 of W_(j div 4).
+ *
+ * Rounding rule: with u = the FP16 spacing at |x| (2^(e-10) for |x| in
+ * [2^e, 2^(e+1)), e >= -14; 2^-24 below 2^-14), lo = u * floor(|x| / u) and
+ * q = |x| / u - floor(|x| / u), the result is sign(x) * (lo + u) if
+ * q + r / 2^16 >= 1, else sign(x) * lo; finite results saturate at 65504.
+ * Averaged over the 2^16 values of r this is |x| to within u / 2^16.
+ * ------------------------------------------------------------------------ */
+
+/* Output number k (0-based) of splitmix64 seeded `seed`: mix(seed + (k+1) * gamma). */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t k);
+
+/* The 16 random bits of direction j of node `node` at sweep t. */
+uint32_t orc_sr_bits(uint64_t seed, uint64_t t, uint64_t node, int j);
+
+/* Stochastic rounding of x to FP16 with random bits r (0..65535). If margin
+ * is not NULL it receives |q + r/2^16 - 1|, the distance of the decision from
+ * its threshold in units of the FP16 spacing (infinite when x is an FP16 value). */
+double orc_round_half_stochastic(double x, uint32_t r, double* margin);
+
+/* The same over arrays: out[k] and margin[k] (margin may be NULL) for x[k], r[k]. */
+void orc_round_half_stochastic_n(const double* x, const uint32_t* r, int64_t n, double* out, double* margin);
+
+/* One push step of the FP16-shifted stochastic format: d_src holds the
+ * deviations at sweep t (0 at half-way solid cells), d_dst receives them at
+ * t+1 (must be zero at half-way solid cells on entry). node_of[N] numbers the
+ * nodes that draw the random bits (NULL: the cell index). margin (NULL, or
+ * double[19][N]) receives, for each slot of d_dst, the margin of the rounding
+ * that produced it (INFINITY where no rounding happened). */
+void orc_step_f16_stochastic(int nx, int ny, int nz, const uint8_t* flags, double omega_plus,
+                             double omega_minus, const double F[3], const double* d_src, double* d_dst,
+                             uint64_t seed, uint64_t t, const int32_t* node_of, double* margin);
+
 /* Threads the OpenMP runtime would use (1 when built without OpenMP). */
 int orc_max_threads(void);
 
