@@ -325,7 +325,8 @@ def accuracy_poiseuille64(lbm, stream):
     profiles = {}
     for name, prec in (("f64", lbm.LBM_F64), ("f64_double_float", lbm.LBM_F64_DOUBLE_FLOAT),
                        ("f32_shifted", lbm.LBM_F32_SHIFTED), ("f16_shifted", lbm.LBM_F16_SHIFTED),
-                       ("f32_shifted_double_float", lbm.LBM_F32_SHIFTED_DOUBLE_FLOAT)):
+                       ("f32_shifted_double_float", lbm.LBM_F32_SHIFTED_DOUBLE_FLOAT),
+                       ("f16_shifted_stochastic", lbm.LBM_F16_SHIFTED_STOCHASTIC)):
         h = lbm.lbm_create_lattice(lbm.make_desc(dims, prec, lbm.LBM_DIRECT, lbm.LBM_AA_INPLACE, (1, 0, 1)), stream)
         try:
             lbm.lbm_set_geometry(h, 0, inputs.channel_flags(*dims))
@@ -380,7 +381,7 @@ def variant(lbm, stream, precision, propagation, steps, nf, peak):
         lbm.lbm_destroy(h)
     mflups = nf * steps / sec / 1e6
     elem = {lbm.LBM_F64: 8, lbm.LBM_F32_SHIFTED: 4, lbm.LBM_F16_SHIFTED: 2, lbm.LBM_F64_DOUBLE_FLOAT: 8,
-            lbm.LBM_F32_SHIFTED_DOUBLE_FLOAT: 4}[precision]
+            lbm.LBM_F32_SHIFTED_DOUBLE_FLOAT: 4, lbm.LBM_F16_SHIFTED_STOCHASTIC: 2}[precision]
     bpf = bytes_per_flup(elem, False, "pull" if propagation == lbm.LBM_PULL_TWO_GRID else "aa")
     gbs = mflups * 1e6 * bpf / 1e9
     return {"mflups": round(mflups, 1), "bytes_per_flup": bpf, "achieved_gbs": round(gbs, 1),
@@ -496,6 +497,8 @@ def run_gpu(args):
                                                     nf, peak)
         variants["f32_shifted_aa"] = variant(lbm, stream, lbm.LBM_F32_SHIFTED, lbm.LBM_AA_INPLACE, vs, nf, peak)
         variants["f16_shifted_aa"] = variant(lbm, stream, lbm.LBM_F16_SHIFTED, lbm.LBM_AA_INPLACE, vs, nf, peak)
+        variants["f16_shifted_stochastic_aa"] = variant(lbm, stream, lbm.LBM_F16_SHIFTED_STOCHASTIC,
+                                                        lbm.LBM_AA_INPLACE, vs, nf, peak)
         variants["f32_shifted_double_float_aa"] = variant(lbm, stream, lbm.LBM_F32_SHIFTED_DOUBLE_FLOAT,
                                                           lbm.LBM_AA_INPLACE, vs, nf, peak)
         c2 = inputs.POROUS_256
@@ -612,7 +615,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep-only", action="store_true", help="profiling: warm-up and timed steps only")
     ap.add_argument("--dims", type=int, default=0, help="profiling: cubic duct of this size instead of 256")
-    ap.add_argument("--precision", default="f64", choices=["f64", "f32", "f16", "f64df", "f32df"],
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32", "f16", "f64df", "f32df", "f16sr"],
                     help="profiling (with --sweep-only)")
     ap.add_argument("--prop", default="aa", choices=["aa", "pull"], help="profiling (with --sweep-only)")
     ap.add_argument("--workload", default="duct", choices=["duct", "porous", "batch"],

@@ -80,13 +80,35 @@ typedef enum {
  *   LBM_F32_SHIFTED_DOUBLE_FLOAT
  *                        f_i - w_i in FP32, collided in double-float and rounded
  *                        once when stored: FP32 bytes, with the accuracy that
- *                        FP32 collision arithmetic loses. */
+ *                        FP32 collision arithmetic loses.
+ *   LBM_F16_SHIFTED_STOCHASTIC
+ *                        f_i - w_i in FP16, FP32 collision, rounded to FP16
+ *                        stochastically: up (away from zero) with the
+ *                        probability of the remainder, from 16 random bits per
+ *                        value. Round-to-nearest FP16 loses every per-step
+ *                        change below half an FP16 spacing (a slow forced flow
+ *                        stagnates); stochastic rounding keeps them on average.
+ *                        The bits come from a counter-based splitmix64 (Steele,
+ *                        Lea and Flood, OOPSLA 2014): node k (the cell index, or
+ *                        the list index under indirect addressing) at sweep t
+ *                        draws key K = output number (t << 32) | k of the stream
+ *                        seeded with the lattice's seed, then outputs 0..3 of the
+ *                        stream seeded with K; with W_0 = K and W_m those
+ *                        outputs, direction j uses bits 16 (j mod 4) .. +15 of
+ *                        W_(j div 4) as r, and rounds away from zero iff the
+ *                        remainder of |x| past the FP16 value below it, in FP16
+ *                        spacings, plus r / 2^16 reaches 1. Finite values beyond
+ *                        65504 saturate. Results do not depend on the launch
+ *                        shape, the propagation pattern or graph replay. The seed
+ *                        and the sweep number are set by
+ *                        lbm_set_stochastic_rounding. */
 typedef enum {
   LBM_F64 = 0,
   LBM_F32_SHIFTED = 1,
   LBM_F16_SHIFTED = 2,
   LBM_F64_DOUBLE_FLOAT = 3,
-  LBM_F32_SHIFTED_DOUBLE_FLOAT = 4
+  LBM_F32_SHIFTED_DOUBLE_FLOAT = 4,
+  LBM_F16_SHIFTED_STOCHASTIC = 5
 } lbm_precision;
 
 /* Full array with flag field (direct) or fluid list + int32 adjacency list
@@ -158,6 +180,17 @@ int lbm_init_equilibrium(lbm_handle h, int32_t lattice, const double* rho, const
  * collide-and-propagate sweep, Sec. 3). Asynchronous on the handle's stream;
  * runs of steps are replayed from captured CUDA graphs. */
 int lbm_step(lbm_handle h, int32_t n);
+
+/* Seed and sweep number of the random bits of LBM_F16_SHIFTED_STOCHASTIC
+ * storage (see lbm_precision). Lattice l of a batch uses seed + l. `sweep` is
+ * the number t that the next time step draws with (t >= 0); every step then
+ * advances it by one. At creation the seed is 0; lbm_init_equilibrium and
+ * lbm_write_pdfs set the sweep number to 0, so to resume a run from a
+ * checkpoint, write the PDFs first and then call this with the saved seed and
+ * step count. Not part of the paper (which stores FP64 only). Returns
+ * LBM_ERR_UNSUPPORTED for handles of any other precision, LBM_ERR_ARG for
+ * sweep < 0. Synchronous. */
+int lbm_set_stochastic_rounding(lbm_handle h, uint64_t seed, int64_t sweep);
 
 /* Wait for all work issued on the handle's stream. */
 int lbm_synchronize(lbm_handle h);

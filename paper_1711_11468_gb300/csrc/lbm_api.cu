@@ -90,6 +90,10 @@ struct lbm_lattice_s {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int* d_status = nullptr;   // kernels set bits here (bounded waits that gave up)
+  // FP16 stochastic format: the seed of lattice 0 (lattice l uses seed + l) and
+  // the pair of sweep counters; word `phase` holds the number of the next sweep.
+  unsigned long long sr_seed = 0;
+  unsigned long long* d_sweep = nullptr;
 
   void* dalloc(size_t n) {
     if (n == 0) n = 256;
@@ -173,7 +177,7 @@ int validate_desc(const lbm_desc* d) {
   if (d->nx < 2 || d->ny < 2 || d->nz < 2) return fail(LBM_ERR_ARG, "every dimension must be >= 2");
   const int64_t N = (int64_t)d->nx * d->ny * d->nz;
   if (N >= ((int64_t)1 << 31)) return fail(LBM_ERR_ARG, "lattice too large: N must be < 2^31 cells");
-  if (d->precision < LBM_F64 || d->precision > LBM_F32_SHIFTED_DOUBLE_FLOAT) return fail(LBM_ERR_ARG, "bad precision");
+  if (d->precision < LBM_F64 || d->precision > LBM_F16_SHIFTED_STOCHASTIC) return fail(LBM_ERR_ARG, "bad precision");
   if (d->addressing != LBM_DIRECT && d->addressing != LBM_INDIRECT) return fail(LBM_ERR_ARG, "bad addressing");
   if (d->propagation != LBM_PULL_TWO_GRID && d->propagation != LBM_AA_INPLACE)
     return fail(LBM_ERR_ARG, "bad propagation");
@@ -239,6 +243,11 @@ int create_impl(const lbm_desc* descs, int32_t count, void* stream, lbm_handle* 
   if (!h->d_status || cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) {
     lbm_destroy(h);
     return fail(LBM_ERR_OOM, "allocation of the status word failed");
+  }
+  h->d_sweep = static_cast<unsigned long long*>(h->dalloc(2 * sizeof(unsigned long long)));
+  if (!h->d_sweep || cudaMemset(h->d_sweep, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+    lbm_destroy(h);
+    return fail(LBM_ERR_OOM, "allocation of the sweep counter failed");
   }
   for (int32_t k = 0; k < count; ++k) {
     Lattice& L = h->lat[k];
@@ -352,6 +361,17 @@ int sm_count() {
   return sms > 0 ? sms : 1;
 }
 
+// The kernel view of lattice k with the stochastic format's stream attached.
+LatticeView sweep_view(lbm_handle h, size_t k) {
+  LatticeView v = h->lat[k].view();
+  v.sr_seed = h->sr_seed + (unsigned long long)k;
+  v.sweep_ctr = h->d_sweep;
+  return v;
+}
+
+// Set the number of the next sweep (device word `phase`), in stream order.
+__global__ void k_set_sweep(unsigned long long* ctr, int phase, unsigned long long value) { ctr[phase] = value; }
+
 // (Re)build the batch descriptor table and the tile work list on the device.
 int build_tables(lbm_handle h) {
   if (!h->tables_dirty) return LBM_OK;
@@ -362,7 +382,7 @@ int build_tables(lbm_handle h) {
   std::vector<BatchTile> tiles;
   for (size_t k = 0; k < h->lat.size(); ++k) {
     Lattice& L = h->lat[k];
-    fill_batch_lattice(h->prec, desc.data() + k * db, L.view(), L.pdf[0], L.pdf[1], L.trt);
+    fill_batch_lattice(h->prec, desc.data() + k * db, sweep_view(h, k), L.pdf[0], L.pdf[1], L.trt);
     for (int64_t first = 0; first < L.nstore; first += tile)
       tiles.push_back(BatchTile{(int32_t)k, (int32_t)std::min<int64_t>(tile, L.nstore - first), first});
   }
@@ -394,16 +414,17 @@ cudaError_t issue_step(lbm_handle h, int phase, cudaStream_t s) {
   if (h->batched()) {
     const SweepKind kind = h->prop == LBM_PULL_TWO_GRID ? kPull : (phase == 0 ? kAAEven : kAAOdd);
     return launch_batch_sweep(h->prec, kind, h->d_lat, h->d_tiles, h->ntiles, h->threads, batch_ctas(h, kind), phase,
-                              s);
+                              h->d_sweep, s);
   }
-  for (Lattice& L : h->lat) {
-    const LatticeView v = L.view();
+  for (size_t k = 0; k < h->lat.size(); ++k) {
+    Lattice& L = h->lat[k];
+    const LatticeView v = sweep_view(h, k);
     cudaError_t e;
     if (h->prop == LBM_PULL_TWO_GRID)
-      e = launch_sweep(v, kPull, L.pdf[phase], L.pdf[phase ^ 1], L.trt, h->threads, h->cells_per_thread, s);
+      e = launch_sweep(v, kPull, phase, L.pdf[phase], L.pdf[phase ^ 1], L.trt, h->threads, h->cells_per_thread, s);
     else
-      e = launch_sweep(v, phase == 0 ? kAAEven : kAAOdd, L.pdf[0], L.pdf[0], L.trt, h->threads, h->cells_per_thread,
-                       s);
+      e = launch_sweep(v, phase == 0 ? kAAEven : kAAOdd, phase, L.pdf[0], L.pdf[0], L.trt, h->threads,
+                       h->cells_per_thread, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -479,6 +500,7 @@ int lbm_destroy(lbm_handle h) {
     h->dfree(L.flags, (size_t)L.N);
   }
   h->dfree(h->d_status, sizeof(int));
+  h->dfree(h->d_sweep, 2 * sizeof(unsigned long long));
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
@@ -544,6 +566,8 @@ int lbm_init_equilibrium(lbm_handle h, int32_t lattice, const double* rho, const
   LBM_CUDA(h, launch_from_canonical(L.view(), current_layout(h), state_buffer(h, L), nullptr,
                                     rho ? r.as<double>() : nullptr, u ? v.as<double>() : nullptr, h->stream),
            "initial state");
+  k_set_sweep<<<1, 1, 0, h->stream>>>(h->d_sweep, h->phase, 0ull);
+  LBM_CUDA(h, cudaGetLastError(), "sweep counter");
   LBM_CUDA(h, cudaStreamSynchronize(h->stream), "init sync");
   L.init = true;
   h->steps = 0;
@@ -562,6 +586,8 @@ int lbm_write_pdfs(lbm_handle h, int32_t lattice, const double* in, size_t in_le
   LBM_CUDA(h, launch_from_canonical(L.view(), current_layout(h), state_buffer(h, L), c.as<double>(), nullptr,
                                     nullptr, h->stream),
            "write state");
+  k_set_sweep<<<1, 1, 0, h->stream>>>(h->d_sweep, h->phase, 0ull);
+  LBM_CUDA(h, cudaGetLastError(), "sweep counter");
   LBM_CUDA(h, cudaStreamSynchronize(h->stream), "write sync");
   L.init = true;
   h->steps = 0;
@@ -573,6 +599,19 @@ int lbm_step(lbm_handle h, int32_t n) {
   if (n < 0) return fail(LBM_ERR_ARG, "n must be >= 0");
   if (int rc = ready_to_step(h)) return rc;
   return step_impl(h, n, true);
+}
+
+int lbm_set_stochastic_rounding(lbm_handle h, uint64_t seed, int64_t sweep) {
+  if (int rc = check_handle(h)) return rc;
+  if (h->prec != LBM_F16_SHIFTED_STOCHASTIC)
+    return fail(LBM_ERR_UNSUPPORTED, "stochastic rounding applies to LBM_F16_SHIFTED_STOCHASTIC storage only");
+  if (sweep < 0) return fail(LBM_ERR_ARG, "the sweep number must be >= 0");
+  h->drop_graphs();   // the seed is part of every captured launch
+  h->sr_seed = seed;
+  k_set_sweep<<<1, 1, 0, h->stream>>>(h->d_sweep, h->phase, (unsigned long long)sweep);
+  LBM_CUDA(h, cudaGetLastError(), "sweep counter");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "sweep counter sync");
+  return LBM_OK;
 }
 
 int lbm_synchronize(lbm_handle h) {
@@ -746,6 +785,10 @@ int lbm_autotune(lbm_handle h, int32_t steps) {
   std::vector<void*> saved(h->lat.size(), nullptr);
   const int phase0 = h->phase;
   const int64_t steps0 = h->steps;
+  unsigned long long sweep0 = 0;
+  LBM_CUDA(h, cudaMemcpyAsync(&sweep0, h->d_sweep + phase0, sizeof(sweep0), cudaMemcpyDeviceToHost, h->stream),
+           "save sweep counter");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "autotune sync");
   for (size_t k = 0; k < h->lat.size(); ++k) {
     Lattice& L = h->lat[k];
     saved[k] = h->dalloc(pdf_bytes(L, h->prec));
@@ -807,6 +850,8 @@ int lbm_autotune(lbm_handle h, int32_t steps) {
                                 h->stream),
              "restore state");
   }
+  k_set_sweep<<<1, 1, 0, h->stream>>>(h->d_sweep, phase0, sweep0);
+  LBM_CUDA(h, cudaGetLastError(), "restore sweep counter");
   LBM_CUDA(h, cudaStreamSynchronize(h->stream), "autotune sync");
   for (size_t k = 0; k < h->lat.size(); ++k) h->dfree(saved[k], pdf_bytes(h->lat[k], h->prec));
   if (h->poisoned) return fail(LBM_ERR_CUDA, "autotune hit a CUDA error");

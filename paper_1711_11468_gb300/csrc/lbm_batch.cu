@@ -10,12 +10,9 @@
 
 namespace lbm {
 
-template <typename S>
-Trt<Arith<S>> trt_as(const TrtParams& p);
-
 namespace {
 
-template <typename A>
+template <typename S>
 struct __align__(16) BatchDesc {
   void* pdf[2];            // state grid(s): AA uses pdf[0]; pull alternates
   const uint8_t* flags;    // [N], full array only
@@ -24,7 +21,7 @@ struct __align__(16) BatchDesc {
   int nx, ny, nz;
   int indirect, has_halfway, small;   // small: N < 2^24 (fast coordinate split)
   float inv_nx, inv_ny;
-  Trt<A> p;
+  ParamsT<S> p;
 };
 
 // n -> (x, y, z) for a full array. For N < 2^24 the quotient through a float
@@ -104,7 +101,7 @@ __device__ __forceinline__ void relax_scatter(const D& sd, int phase, const Node
   if (KIND == kPull && !sd.indirect && sd.flags[(int)r.node] == kSolidFullway)
     reverse(f);
   else
-    Storage<S>::relax(f, sd.p);
+    Storage<S>::relax(f, sd.p, (uint32_t)r.node);
   if (KIND == kAAEven) {
     S* pdf = static_cast<S*>(sd.pdf[0]);
 #pragma unroll
@@ -127,12 +124,21 @@ __device__ __forceinline__ void relax_scatter(const D& sd, int phase, const Node
 // j + blockDim.x) and issues both nodes' loads before colliding either: a
 // node's loads cannot otherwise start before the previous node's stores, since
 // both touch the same arrays.
+// The stochastic format numbers the sweeps in ctr (see begin_sweep): every
+// lattice of the batch is at the same sweep, and lattice l draws from its own
+// seed, the handle's seed + l.
 template <typename S, int KIND>
-__global__ void __launch_bounds__(512) k_batch(const BatchDesc<Arith<S>>* __restrict__ lat,
-                                               const BatchTile* __restrict__ tiles, int ntiles, int phase) {
-  using A = Arith<S>;
-  using D = BatchDesc<A>;
+__global__ void __launch_bounds__(512) k_batch(const BatchDesc<S>* __restrict__ lat,
+                                               const BatchTile* __restrict__ tiles, int ntiles, int phase,
+                                               unsigned long long* ctr) {
+  using D = BatchDesc<S>;
+  constexpr bool kSr = std::is_same<S, h16sr>::value;
   __shared__ D sd;
+  unsigned long long sweep = 0;
+  if constexpr (kSr) {
+    sweep = ctr[phase];
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr[phase ^ 1] = sweep + 1;
+  }
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const BatchTile tile = tiles[t];
     __syncthreads();   // the previous tile is done with sd
@@ -142,6 +148,10 @@ __global__ void __launch_bounds__(512) k_batch(const BatchDesc<Arith<S>>* __rest
       for (int w = threadIdx.x; w < (int)(sizeof(D) / sizeof(int4)); w += blockDim.x) dst[w] = src[w];
     }
     __syncthreads();
+    if constexpr (kSr) {
+      if (threadIdx.x == 0) sd.p.base = sd.p.seed + kSplitmixGamma * (1ull + (sweep << 32));
+      __syncthreads();
+    }
     // pairs only where a node's 19 values fit in 19 registers (FP32 and FP16 raw values)
     constexpr bool kPairs = sizeof(RawT<S>) == 4;
     for (int j = threadIdx.x; j < tile.count; j += (kPairs ? 2 : 1) * blockDim.x) {
@@ -165,22 +175,22 @@ __global__ void __launch_bounds__(512) k_batch(const BatchDesc<Arith<S>>* __rest
 
 template <typename S>
 cudaError_t batch_typed(SweepKind kind, const void* d_lat, const BatchTile* d_tiles, int ntiles, int threads,
-                        int ctas, int phase, cudaStream_t s) {
-  using D = BatchDesc<Arith<S>>;
+                        int ctas, int phase, unsigned long long* ctr, cudaStream_t s) {
+  using D = BatchDesc<S>;
   const D* lat = static_cast<const D*>(d_lat);
   if (ntiles <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)(ctas > 0 ? std::min(ctas, ntiles) : ntiles);
   switch (kind) {
-    case kPull: k_batch<S, kPull><<<grid, threads, 0, s>>>(lat, d_tiles, ntiles, phase); break;
-    case kAAEven: k_batch<S, kAAEven><<<grid, threads, 0, s>>>(lat, d_tiles, ntiles, phase); break;
-    case kAAOdd: k_batch<S, kAAOdd><<<grid, threads, 0, s>>>(lat, d_tiles, ntiles, phase); break;
+    case kPull: k_batch<S, kPull><<<grid, threads, 0, s>>>(lat, d_tiles, ntiles, phase, ctr); break;
+    case kAAEven: k_batch<S, kAAEven><<<grid, threads, 0, s>>>(lat, d_tiles, ntiles, phase, ctr); break;
+    case kAAOdd: k_batch<S, kAAOdd><<<grid, threads, 0, s>>>(lat, d_tiles, ntiles, phase, ctr); break;
   }
   return cudaGetLastError();
 }
 
 template <typename S>
 void fill_typed(void* host_desc, const LatticeView& v, void* pdf_a, void* pdf_b, const TrtParams& p) {
-  using D = BatchDesc<Arith<S>>;
+  using D = BatchDesc<S>;
   D d{};
   d.pdf[0] = pdf_a;
   d.pdf[1] = pdf_b;
@@ -195,15 +205,21 @@ void fill_typed(void* host_desc, const LatticeView& v, void* pdf_a, void* pdf_b,
   d.small = v.n_cells < (int64_t(1) << 24) ? 1 : 0;
   d.inv_nx = 1.0f / (float)v.nx;
   d.inv_ny = 1.0f / (float)v.ny;
-  d.p = trt_as<S>(p);
+  d.p = params_as<S>(p, v, 0);
   *static_cast<D*>(host_desc) = d;
 }
 
 }  // namespace
 
 size_t batch_lattice_bytes(int prec) {
-  return prec == kF64 ? sizeof(BatchDesc<double>)
-                      : ((prec == kF64DF || prec == kF32DF) ? sizeof(BatchDesc<df32>) : sizeof(BatchDesc<float>));
+  switch (prec) {
+    case kF64: return sizeof(BatchDesc<double>);
+    case kF32: return sizeof(BatchDesc<float>);
+    case kF64DF: return sizeof(BatchDesc<f64df>);
+    case kF32DF: return sizeof(BatchDesc<f32df>);
+    case kF16SR: return sizeof(BatchDesc<h16sr>);
+    default: return sizeof(BatchDesc<__half>);
+  }
 }
 
 void fill_batch_lattice(int prec, void* host_desc, const LatticeView& v, void* pdf_a, void* pdf_b,
@@ -213,6 +229,7 @@ void fill_batch_lattice(int prec, void* host_desc, const LatticeView& v, void* p
     case kF32: fill_typed<float>(host_desc, v, pdf_a, pdf_b, p); break;
     case kF64DF: fill_typed<f64df>(host_desc, v, pdf_a, pdf_b, p); break;
     case kF32DF: fill_typed<f32df>(host_desc, v, pdf_a, pdf_b, p); break;
+    case kF16SR: fill_typed<h16sr>(host_desc, v, pdf_a, pdf_b, p); break;
     default: fill_typed<__half>(host_desc, v, pdf_a, pdf_b, p); break;
   }
 }
@@ -227,19 +244,22 @@ int batch_blocks_per_sm(int prec, SweepKind kind, int threads) {
     case kAAOdd: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<S, kAAOdd>, threads, 0); break; \
   }
   if (prec == kF64) { LBM_OCC(double) } else if (prec == kF32) { LBM_OCC(float) }
-  else if (prec == kF64DF) { LBM_OCC(f64df) } else if (prec == kF32DF) { LBM_OCC(f32df) } else { LBM_OCC(__half) }
+  else if (prec == kF64DF) { LBM_OCC(f64df) } else if (prec == kF32DF) { LBM_OCC(f32df) }
+  else if (prec == kF16SR) { LBM_OCC(h16sr) } else { LBM_OCC(__half) }
 #undef LBM_OCC
   return e == cudaSuccess && n > 0 ? n : 1;
 }
 
 cudaError_t launch_batch_sweep(int prec, SweepKind kind, const void* d_lattices, const BatchTile* d_tiles,
-                               int32_t n_tiles, int threads, int ctas, int phase, cudaStream_t s) {
+                               int32_t n_tiles, int threads, int ctas, int phase, unsigned long long* ctr,
+                               cudaStream_t s) {
   switch (prec) {
-    case kF64: return batch_typed<double>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, s);
-    case kF32: return batch_typed<float>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, s);
-    case kF16: return batch_typed<__half>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, s);
-    case kF64DF: return batch_typed<f64df>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, s);
-    case kF32DF: return batch_typed<f32df>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, s);
+    case kF64: return batch_typed<double>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, ctr, s);
+    case kF32: return batch_typed<float>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, ctr, s);
+    case kF16: return batch_typed<__half>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, ctr, s);
+    case kF64DF: return batch_typed<f64df>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, ctr, s);
+    case kF32DF: return batch_typed<f32df>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, ctr, s);
+    case kF16SR: return batch_typed<h16sr>(kind, d_lattices, d_tiles, n_tiles, threads, ctas, phase, ctr, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -21,7 +21,7 @@ namespace lbm {
 //               half-way link). The AA pattern after an odd number of steps.
 enum Layout : int { kCanonical = 0, kPullForm = 1, kAAForm = 2 };
 
-enum Prec : int { kF64 = 0, kF32 = 1, kF16 = 2, kF64DF = 3, kF32DF = 4 };
+enum Prec : int { kF64 = 0, kF32 = 1, kF16 = 2, kF64DF = 3, kF32DF = 4, kF16SR = 5 };
 
 enum SweepKind : int { kPull = 0, kAAEven = 1, kAAOdd = 2 };
 
@@ -47,6 +47,10 @@ struct LatticeView {
   const int32_t* cell_of = nullptr;   // [Nf], indirect only
   const int32_t* list_index = nullptr;  // [N] node of each cell or -1, indirect only
   int* status = nullptr;                // device status word of the handle (timeouts)
+  // FP16 stochastic format only: the lattice's seed and the handle's pair of
+  // sweep counters (a sweep of parity q reads word q and writes word q ^ 1).
+  unsigned long long sr_seed = 0;
+  unsigned long long* sweep_ctr = nullptr;
 };
 
 struct TrtParams {
@@ -57,8 +61,8 @@ struct TrtParams {
 
 // ------------------------------------------------------------ sweep launchers
 // One time step of one lattice. src == dst for the AA kinds. cells_per_thread
-// (1 or 2) applies to full arrays.
-cudaError_t launch_sweep(const LatticeView& v, SweepKind kind, const void* src, void* dst,
+// (1 or 2) applies to full arrays. parity: the step count mod 2.
+cudaError_t launch_sweep(const LatticeView& v, SweepKind kind, int parity, const void* src, void* dst,
                          const TrtParams& p, int threads, int cells_per_thread, cudaStream_t s);
 
 
@@ -75,7 +79,8 @@ size_t batch_lattice_bytes(int prec);
 void fill_batch_lattice(int prec, void* host_desc, const LatticeView& v, void* pdf_a, void* pdf_b,
                         const TrtParams& p);
 cudaError_t launch_batch_sweep(int prec, SweepKind kind, const void* d_lattices, const BatchTile* d_tiles,
-                               int32_t n_tiles, int threads, int ctas, int phase, cudaStream_t s);
+                               int32_t n_tiles, int threads, int ctas, int phase, unsigned long long* sweep_ctr,
+                               cudaStream_t s);
 // Resident CTAs of the batched kernel per SM at this block size (occupancy).
 int batch_blocks_per_sm(int prec, SweepKind kind, int threads);
 

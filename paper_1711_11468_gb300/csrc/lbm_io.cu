@@ -286,6 +286,7 @@ unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
     case kF16: { using S = __half; __VA_ARGS__; break; }        \
     case kF64DF: { using S = f64df; __VA_ARGS__; break; }       \
     case kF32DF: { using S = f32df; __VA_ARGS__; break; }       \
+    case kF16SR: { using S = h16sr; __VA_ARGS__; break; }       \
     default: return cudaErrorInvalidValue;                      \
   }
 

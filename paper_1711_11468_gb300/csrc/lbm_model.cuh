@@ -12,6 +12,7 @@
 #include <cstdint>
 
 #include "lbm_df32.cuh"
+#include "lbm_sr.cuh"
 
 namespace lbm {
 
@@ -63,6 +64,18 @@ struct Trt {
   A a, b, rest, wp_w0;
   A wp_w[2], c4[2], c3[2];
   A fk[9];
+};
+
+// TRT parameters of the stochastically rounded FP16 format plus its random
+// stream: the lattice's seed, the device word pair that numbers the sweeps
+// (ctr[parity] holds this sweep's number t; the sweep writes t + 1 into
+// ctr[parity ^ 1], which the next sweep, of the other parity, reads) and the
+// per-sweep base seed + gamma (1 + (t << 32)), set on the device.
+struct TrtSr : Trt<float> {
+  unsigned long long seed;
+  unsigned long long base;
+  unsigned long long* ctr;
+  int parity;
 };
 
 // ---------------------------------------------------------------- collision
@@ -129,6 +142,12 @@ __device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
 //            once on store. FP32 collision arithmetic makes correlated
 //            rounding errors that accumulate over steps; rounding a precisely
 //            collided value only at the store does not.
+//   h16sr  : d_i = f_i - w_i in FP16, collided in FP32, rounded to FP16
+//            stochastically (lbm_sr.cuh) with the random bits of the node.
+//            Raw values are the FP16 bit patterns, so that moving them (and
+//            reversing them at full-way solids) needs no conversion.
+// relax(f, p, node) is the entry point of the sweeps; node numbers the node's
+// random stream and only h16sr uses it.
 // The shift keeps the collided magnitudes near the small departures that carry
 // the flow instead of near w_i.
 struct f64df {
@@ -137,36 +156,46 @@ struct f64df {
 struct f32df {
   float v;
 };
+struct h16sr {
+  __half v;
+};
 
 template <typename S>
 struct Storage;
 
 template <>
 struct Storage<double> {
+  using Params = Trt<double>;
   using Raw = double;
   using A = double;
   static constexpr bool kShifted = false, kIncrement = false;
   __device__ __forceinline__ static Raw load(const double* p) { return __ldcs(p); }
   __device__ __forceinline__ static void store(double* p, Raw v) { __stcs(p, v); }
-  __device__ __forceinline__ static void relax(Raw (&f)[Q], const Trt<A>& p) { collide<A, false>(f, p); }
+  __device__ __forceinline__ static void relax(Raw (&f)[Q], const Params& p, uint32_t = 0) {
+    collide<A, false>(f, p);
+  }
   __device__ __forceinline__ static double to_f64(double v, int) { return v; }
   __device__ __forceinline__ static double from_f64(double f, int) { return f; }
 };
 
 template <>
 struct Storage<float> {
+  using Params = Trt<float>;
   using Raw = float;
   using A = float;
   static constexpr bool kShifted = true, kIncrement = false;
   __device__ __forceinline__ static Raw load(const float* p) { return __ldcs(p); }
   __device__ __forceinline__ static void store(float* p, Raw v) { __stcs(p, v); }
-  __device__ __forceinline__ static void relax(Raw (&f)[Q], const Trt<A>& p) { collide<A, true>(f, p); }
+  __device__ __forceinline__ static void relax(Raw (&f)[Q], const Params& p, uint32_t = 0) {
+    collide<A, true>(f, p);
+  }
   __device__ __forceinline__ static double to_f64(float v, int i) { return weight(i) + (double)v; }
   __device__ __forceinline__ static float from_f64(double f, int i) { return __double2float_rn(f - weight(i)); }
 };
 
 template <>
 struct Storage<__half> {
+  using Params = Trt<float>;
   using Raw = float;
   using A = float;
   static constexpr bool kShifted = true, kIncrement = false;
@@ -176,7 +205,9 @@ struct Storage<__half> {
   __device__ __forceinline__ static void store(__half* p, Raw v) {
     __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(__float2half_rn(v)));
   }
-  __device__ __forceinline__ static void relax(Raw (&f)[Q], const Trt<A>& p) { collide<A, true>(f, p); }
+  __device__ __forceinline__ static void relax(Raw (&f)[Q], const Params& p, uint32_t = 0) {
+    collide<A, true>(f, p);
+  }
   __device__ __forceinline__ static double to_f64(__half v, int i) { return weight(i) + (double)__half2float(v); }
   __device__ __forceinline__ static __half from_f64(double f, int i) {
     // FP64 -> FP16 in one rounding (a detour through FP32 could double-round).
@@ -186,12 +217,13 @@ struct Storage<__half> {
 
 template <>
 struct Storage<f64df> {
+  using Params = Trt<df32>;
   using Raw = double;
   using A = df32;
   static constexpr bool kShifted = true, kIncrement = true;
   __device__ __forceinline__ static Raw load(const f64df* p) { return __ldcs(reinterpret_cast<const double*>(p)); }
   __device__ __forceinline__ static void store(f64df* p, Raw v) { __stcs(reinterpret_cast<double*>(p), v); }
-  __device__ __forceinline__ static void relax(Raw (&f)[Q], const Trt<A>& p) {
+  __device__ __forceinline__ static void relax(Raw (&f)[Q], const Params& p, uint32_t = 0) {
     df32 d[Q];
     bool out_of_range = false;
 #pragma unroll
@@ -210,12 +242,13 @@ struct Storage<f64df> {
 
 template <>
 struct Storage<f32df> {
+  using Params = Trt<df32>;
   using Raw = float;
   using A = df32;
   static constexpr bool kShifted = true, kIncrement = false;
   __device__ __forceinline__ static Raw load(const f32df* p) { return __ldcs(reinterpret_cast<const float*>(p)); }
   __device__ __forceinline__ static void store(f32df* p, Raw v) { __stcs(reinterpret_cast<float*>(p), v); }
-  __device__ __forceinline__ static void relax(Raw (&f)[Q], const Trt<A>& p) {
+  __device__ __forceinline__ static void relax(Raw (&f)[Q], const Params& p, uint32_t = 0) {
     df32 d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = df32(f[i]);
@@ -226,6 +259,48 @@ struct Storage<f32df> {
   __device__ __forceinline__ static double to_f64(f32df v, int i) { return weight(i) + (double)v.v; }
   __device__ __forceinline__ static f32df from_f64(double f, int i) { return f32df{__double2float_rn(f - weight(i))}; }
 };
+
+template <>
+struct Storage<h16sr> {
+  using Raw = uint32_t;   // the FP16 bit pattern in the low half
+  using A = float;
+  using Params = TrtSr;
+  static constexpr bool kShifted = true, kIncrement = false;
+  __device__ __forceinline__ static Raw load(const h16sr* p) {
+    return __ldcs(reinterpret_cast<const unsigned short*>(p));
+  }
+  __device__ __forceinline__ static void store(h16sr* p, Raw v) {
+    __stcs(reinterpret_cast<unsigned short*>(p), (unsigned short)v);
+  }
+  __device__ __forceinline__ static void relax(Raw (&f)[Q], const Params& p, uint32_t node) {
+    float d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = __half2float(__ushort_as_half((unsigned short)f[i]));
+    collide<float, true>(d, p);
+    unsigned long long w[5];
+    sr_words(p.base, node, w);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = round_half_stochastic(d[i], sr_fraction(w, i));
+  }
+  __device__ __forceinline__ static double to_f64(h16sr v, int i) { return weight(i) + (double)__half2float(v.v); }
+  __device__ __forceinline__ static h16sr from_f64(double f, int i) { return h16sr{__double2half(f - weight(i))}; }
+};
+
+// Per-sweep set-up of the launch parameters. Every thread of the launch calls
+// it first; for the stochastic format it reads the sweep number and the launch's
+// first thread advances the counter of the other parity.
+template <typename S>
+__device__ __forceinline__ typename Storage<S>::Params begin_sweep(const typename Storage<S>::Params& p) {
+  return p;
+}
+template <>
+__device__ __forceinline__ TrtSr begin_sweep<h16sr>(const TrtSr& p) {
+  TrtSr q = p;
+  const unsigned long long t = p.ctr[p.parity];
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) p.ctr[p.parity ^ 1] = t + 1;
+  q.base = p.seed + kSplitmixGamma * (1ull + (t << 32));
+  return q;
+}
 
 // Equilibrium in FP64, absolute or shifted by w_i (initialisation only).
 __device__ __forceinline__ double equilibrium_f64(int i, double rho, double ux, double uy, double uz,

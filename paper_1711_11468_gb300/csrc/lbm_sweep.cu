@@ -38,6 +38,7 @@ template Trt<float> trt_as<float>(const TrtParams&);
 template Trt<float> trt_as<__half>(const TrtParams&);
 template Trt<df32> trt_as<f64df>(const TrtParams&);
 template Trt<df32> trt_as<f32df>(const TrtParams&);
+template Trt<float> trt_as<h16sr>(const TrtParams&);
 
 namespace {
 
@@ -46,7 +47,8 @@ namespace {
 template <typename S, bool kHW>
 __global__ void __launch_bounds__(512) k_dense_pull(const S* __restrict__ src, S* __restrict__ dst,
                                                     const uint8_t* __restrict__ flags, int nx, int ny, int nz,
-                                                    int64_t stride, Trt<Arith<S>> p) {
+                                                    int64_t stride, ParamsT<S> lp) {
+  const ParamsT<S> p = begin_sweep<S>(lp);
   const int x = blockIdx.y * blockDim.x + threadIdx.x;
   if (x >= nx) return;
   const int row = blockIdx.x;
@@ -56,7 +58,8 @@ __global__ void __launch_bounds__(512) k_dense_pull(const S* __restrict__ src, S
 
 template <typename S>
 __global__ void __launch_bounds__(512) k_dense_aa_even(S* __restrict__ pdf, const uint8_t* __restrict__ flags,
-                                                       int nx, int64_t stride, Trt<Arith<S>> p) {
+                                                       int nx, int64_t stride, ParamsT<S> lp) {
+  const ParamsT<S> p = begin_sweep<S>(lp);
   const int x = blockIdx.y * blockDim.x + threadIdx.x;
   if (x >= nx) return;
   const int n = x + nx * (int)blockIdx.x;
@@ -66,7 +69,8 @@ __global__ void __launch_bounds__(512) k_dense_aa_even(S* __restrict__ pdf, cons
 
 template <typename S, bool kHW>
 __global__ void __launch_bounds__(512) k_dense_aa_odd(S* __restrict__ pdf, const uint8_t* __restrict__ flags,
-                                                      int nx, int ny, int nz, int64_t stride, Trt<Arith<S>> p) {
+                                                      int nx, int ny, int nz, int64_t stride, ParamsT<S> lp) {
+  const ParamsT<S> p = begin_sweep<S>(lp);
   const int x = blockIdx.y * blockDim.x + threadIdx.x;
   if (x >= nx) return;
   const int row = blockIdx.x;
@@ -81,7 +85,8 @@ __global__ void __launch_bounds__(512) k_dense_aa_odd(S* __restrict__ pdf, const
 template <typename S, bool kHW>
 __global__ void __launch_bounds__(512) k_dense_pull2(const S* __restrict__ src, S* __restrict__ dst,
                                                      const uint8_t* __restrict__ flags, int nx, int ny, int nz,
-                                                     int64_t stride, Trt<Arith<S>> p) {
+                                                     int64_t stride, ParamsT<S> lp) {
+  const ParamsT<S> p = begin_sweep<S>(lp);
   const int xa = blockIdx.y * 2 * blockDim.x + threadIdx.x, xb = xa + blockDim.x;
   if (xa >= nx) return;
   const int row = blockIdx.x;
@@ -93,12 +98,12 @@ __global__ void __launch_bounds__(512) k_dense_pull2(const S* __restrict__ src, 
   if (fa != kSolidHalfway) pull_dense_gather<S, kHW>(src, flags, Nbr(xa, y, z, nx, ny, nz), na, stride, f);
   if (fb != kSolidHalfway) pull_dense_gather<S, kHW>(src, flags, Nbr(xb, y, z, nx, ny, nz), nb_, stride, g);
   if (fa != kSolidHalfway) {
-    if (fa == kSolidFullway) reverse(f); else Storage<S>::relax(f, p);
+    if (fa == kSolidFullway) reverse(f); else Storage<S>::relax(f, p, (uint32_t)na);
 #pragma unroll
     for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + na, f[i]);
   }
   if (fb != kSolidHalfway) {
-    if (fb == kSolidFullway) reverse(g); else Storage<S>::relax(g, p);
+    if (fb == kSolidFullway) reverse(g); else Storage<S>::relax(g, p, (uint32_t)nb_);
 #pragma unroll
     for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + nb_, g[i]);
   }
@@ -106,7 +111,8 @@ __global__ void __launch_bounds__(512) k_dense_pull2(const S* __restrict__ src, 
 
 template <typename S>
 __global__ void __launch_bounds__(512) k_dense_aa_even2(S* __restrict__ pdf, const uint8_t* __restrict__ flags,
-                                                        int nx, int64_t stride, Trt<Arith<S>> p) {
+                                                        int nx, int64_t stride, ParamsT<S> lp) {
+  const ParamsT<S> p = begin_sweep<S>(lp);
   const int xa = blockIdx.y * 2 * blockDim.x + threadIdx.x, xb = xa + blockDim.x;
   if (xa >= nx) return;
   const int na = xa + nx * (int)blockIdx.x, nb_ = xb + nx * (int)blockIdx.x;
@@ -119,12 +125,12 @@ __global__ void __launch_bounds__(512) k_dense_aa_even2(S* __restrict__ pdf, con
 #pragma unroll
     for (int i = 0; i < Q; ++i) g[i] = Storage<S>::load(dir(pdf, i, stride) + nb_);
   if (ua) {
-    Storage<S>::relax(f, p);
+    Storage<S>::relax(f, p, (uint32_t)na);
 #pragma unroll
     for (int i = 0; i < Q; ++i) Storage<S>::store(dir(pdf, opp(i), stride) + na, f[i]);
   }
   if (ub) {
-    Storage<S>::relax(g, p);
+    Storage<S>::relax(g, p, (uint32_t)nb_);
 #pragma unroll
     for (int i = 0; i < Q; ++i) Storage<S>::store(dir(pdf, opp(i), stride) + nb_, g[i]);
   }
@@ -132,7 +138,8 @@ __global__ void __launch_bounds__(512) k_dense_aa_even2(S* __restrict__ pdf, con
 
 template <typename S, bool kHW>
 __global__ void __launch_bounds__(512) k_dense_aa_odd2(S* __restrict__ pdf, const uint8_t* __restrict__ flags,
-                                                       int nx, int ny, int nz, int64_t stride, Trt<Arith<S>> p) {
+                                                       int nx, int ny, int nz, int64_t stride, ParamsT<S> lp) {
+  const ParamsT<S> p = begin_sweep<S>(lp);
   const int xa = blockIdx.y * 2 * blockDim.x + threadIdx.x, xb = xa + blockDim.x;
   if (xa >= nx) return;
   const int row = blockIdx.x;
@@ -144,11 +151,11 @@ __global__ void __launch_bounds__(512) k_dense_aa_odd2(S* __restrict__ pdf, cons
   if (ua) aa_odd_dense_gather<S, kHW>(pdf, flags, ba, na, stride, f);
   if (ub) aa_odd_dense_gather<S, kHW>(pdf, flags, bb, nb_, stride, g);
   if (ua) {
-    Storage<S>::relax(f, p);
+    Storage<S>::relax(f, p, (uint32_t)na);
     aa_odd_dense_scatter<S, kHW>(pdf, flags, ba, na, stride, f);
   }
   if (ub) {
-    Storage<S>::relax(g, p);
+    Storage<S>::relax(g, p, (uint32_t)nb_);
     aa_odd_dense_scatter<S, kHW>(pdf, flags, bb, nb_, stride, g);
   }
 }
@@ -185,6 +192,17 @@ struct PairIO<float> {
   }
 };
 template <>
+struct PairIO<h16sr> {   // raw values are the bit patterns: no conversion
+  __device__ __forceinline__ static void load(const h16sr* p, uint32_t& a, uint32_t& b) {
+    const unsigned u = __ldcs(reinterpret_cast<const unsigned*>(p));
+    a = u & 0xFFFFu;
+    b = u >> 16;
+  }
+  __device__ __forceinline__ static void store(h16sr* p, uint32_t a, uint32_t b) {
+    __stcs(reinterpret_cast<unsigned*>(p), a | (b << 16));
+  }
+};
+template <>
 struct PairIO<f32df> {
   __device__ __forceinline__ static void load(const f32df* p, float& a, float& b) {
     PairIO<float>::load(reinterpret_cast<const float*>(p), a, b);
@@ -196,7 +214,8 @@ struct PairIO<f32df> {
 
 template <typename S>
 __global__ void __launch_bounds__(512) k_dense_aa_even_pair(S* __restrict__ pdf, const uint8_t* __restrict__ flags,
-                                                            int nx, int64_t stride, Trt<Arith<S>> p) {
+                                                            int nx, int64_t stride, ParamsT<S> lp) {
+  const ParamsT<S> p = begin_sweep<S>(lp);
   const int x = 2 * (blockIdx.y * blockDim.x + threadIdx.x);
   if (x >= nx) return;
   const int n = x + nx * (int)blockIdx.x;
@@ -205,8 +224,8 @@ __global__ void __launch_bounds__(512) k_dense_aa_even_pair(S* __restrict__ pdf,
   RawT<S> f[Q], g[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) PairIO<S>::load(dir(pdf, i, stride) + n, f[i], g[i]);
-  if (ua) Storage<S>::relax(f, p); else reverse(f);
-  if (ub) Storage<S>::relax(g, p); else reverse(g);
+  if (ua) Storage<S>::relax(f, p, (uint32_t)n); else reverse(f);
+  if (ub) Storage<S>::relax(g, p, (uint32_t)(n + 1)); else reverse(g);
 #pragma unroll
   for (int i = 0; i < Q; ++i) PairIO<S>::store(dir(pdf, opp(i), stride) + n, f[i], g[i]);
 }
@@ -218,7 +237,8 @@ __global__ void __launch_bounds__(512) k_dense_aa_even_pair(S* __restrict__ pdf,
 // per-cell bodies. Full arrays without half-way solids only.
 template <typename S>
 __global__ void __launch_bounds__(512) k_dense_aa_odd_pair(S* __restrict__ pdf, const uint8_t* __restrict__ flags,
-                                                           int nx, int ny, int nz, int64_t stride, Trt<Arith<S>> p) {
+                                                           int nx, int ny, int nz, int64_t stride, ParamsT<S> lp) {
+  const ParamsT<S> p = begin_sweep<S>(lp);
   const int x = 2 * (blockIdx.y * blockDim.x + threadIdx.x);
   if (x >= nx) return;
   const int row = blockIdx.x;
@@ -231,12 +251,12 @@ __global__ void __launch_bounds__(512) k_dense_aa_odd_pair(S* __restrict__ pdf, 
   if (!(ua && ub)) {
     if (ua) {
       aa_odd_dense_gather<S, false>(pdf, flags, na, n, stride, f);
-      Storage<S>::relax(f, p);
+      Storage<S>::relax(f, p, (uint32_t)n);
       aa_odd_dense_scatter<S, false>(pdf, flags, na, n, stride, f);
     }
     if (ub) {
       aa_odd_dense_gather<S, false>(pdf, flags, nb, n + 1, stride, g);
-      Storage<S>::relax(g, p);
+      Storage<S>::relax(g, p, (uint32_t)(n + 1));
       aa_odd_dense_scatter<S, false>(pdf, flags, nb, n + 1, stride, g);
     }
     return;
@@ -250,8 +270,8 @@ __global__ void __launch_bounds__(512) k_dense_aa_odd_pair(S* __restrict__ pdf, 
       g[i] = Storage<S>::load(dir(pdf, opp(i), stride) + n + 1 + nb.up(i));
     }
   }
-  Storage<S>::relax(f, p);
-  Storage<S>::relax(g, p);
+  Storage<S>::relax(f, p, (uint32_t)n);
+  Storage<S>::relax(g, p, (uint32_t)(n + 1));
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if (cx(i) == 0) {
@@ -266,7 +286,8 @@ __global__ void __launch_bounds__(512) k_dense_aa_odd_pair(S* __restrict__ pdf, 
 template <typename S>
 __global__ void __launch_bounds__(512) k_dense_pull_pair(const S* __restrict__ src, S* __restrict__ dst,
                                                          const uint8_t* __restrict__ flags, int nx, int ny, int nz,
-                                                         int64_t stride, Trt<Arith<S>> p) {
+                                                         int64_t stride, ParamsT<S> lp) {
+  const ParamsT<S> p = begin_sweep<S>(lp);
   const int x = 2 * (blockIdx.y * blockDim.x + threadIdx.x);
   if (x >= nx) return;
   const int row = blockIdx.x;
@@ -285,21 +306,22 @@ __global__ void __launch_bounds__(512) k_dense_pull_pair(const S* __restrict__ s
     }
   }
   // full arrays without half-way solids: every cell holds PDFs (fluid collides, solid reverses)
-  if (fa == kSolidFullway) reverse(f); else Storage<S>::relax(f, p);
-  if (fb == kSolidFullway) reverse(g); else Storage<S>::relax(g, p);
+  if (fa == kSolidFullway) reverse(f); else Storage<S>::relax(f, p, (uint32_t)n);
+  if (fb == kSolidFullway) reverse(g); else Storage<S>::relax(g, p, (uint32_t)(n + 1));
 #pragma unroll
   for (int i = 0; i < Q; ++i) PairIO<S>::store(dir(dst, i, stride) + n, f[i], g[i]);
 }
 
 template <typename S>
 constexpr bool kHasPairIO = std::is_same<S, __half>::value || std::is_same<S, float>::value ||
-                            std::is_same<S, f32df>::value;
+                            std::is_same<S, f32df>::value || std::is_same<S, h16sr>::value;
 
 // ------------------------------------------------------------ fluid list
 template <typename S>
 __global__ void __launch_bounds__(512) k_list_pull(const S* __restrict__ src, S* __restrict__ dst,
                                                    const uint32_t* __restrict__ link, int64_t nf, int64_t stride,
-                                                   Trt<Arith<S>> p) {
+                                                   ParamsT<S> lp) {
+  const ParamsT<S> p = begin_sweep<S>(lp);
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nf) return;
   pull_list_node<S>(src, dst, link, k, stride, p);
@@ -307,7 +329,8 @@ __global__ void __launch_bounds__(512) k_list_pull(const S* __restrict__ src, S*
 
 template <typename S>
 __global__ void __launch_bounds__(512) k_list_aa_even(S* __restrict__ pdf, int64_t nf, int64_t stride,
-                                                      Trt<Arith<S>> p) {
+                                                      ParamsT<S> lp) {
+  const ParamsT<S> p = begin_sweep<S>(lp);
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nf) return;
   aa_even_node<S>(pdf, k, stride, p);
@@ -315,7 +338,8 @@ __global__ void __launch_bounds__(512) k_list_aa_even(S* __restrict__ pdf, int64
 
 template <typename S>
 __global__ void __launch_bounds__(512) k_list_aa_odd(S* __restrict__ pdf, const uint32_t* __restrict__ link,
-                                                     int64_t nf, int64_t stride, Trt<Arith<S>> p) {
+                                                     int64_t nf, int64_t stride, ParamsT<S> lp) {
+  const ParamsT<S> p = begin_sweep<S>(lp);
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nf) return;
   aa_odd_list_node<S>(pdf, link, k, stride, p);
@@ -333,7 +357,8 @@ constexpr size_t staged_smem_bytes(int threads) { return (size_t)2 * 18 * thread
 template <typename S, int KIND>
 __global__ void __launch_bounds__(kStagedMaxThreads) k_list_staged(const S* __restrict__ src, S* __restrict__ dst,
                                                                    const uint32_t* __restrict__ link, int64_t nf,
-                                                                   int64_t stride, Trt<Arith<S>> p, int* status) {
+                                                                   int64_t stride, ParamsT<S> lp, int* status) {
+  const ParamsT<S> p = begin_sweep<S>(lp);
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar[2];
   __shared__ int abort_flag;
@@ -414,11 +439,11 @@ int staged_grid(int threads, int64_t ntiles) {
 }
 
 template <typename S>
-cudaError_t sweep_typed(const LatticeView& v, SweepKind kind, const void* src_, void* dst_, const TrtParams& tp,
-                        int threads, int cells_per_thread, cudaStream_t s) {
+cudaError_t sweep_typed(const LatticeView& v, SweepKind kind, int parity, const void* src_, void* dst_,
+                        const TrtParams& tp, int threads, int cells_per_thread, cudaStream_t s) {
   const S* src = static_cast<const S*>(src_);
   S* dst = static_cast<S*>(dst_);
-  const Trt<Arith<S>> p = trt_as<S>(tp);
+  const ParamsT<S> p = params_as<S>(tp, v, parity);
   if (threads <= 0) threads = 256;
   if (!v.indirect && cells_per_thread == 2) {
     const int bx = std::min(threads, ((v.nx / 2 + 31) / 32) * 32);
@@ -510,14 +535,15 @@ cudaError_t sweep_typed(const LatticeView& v, SweepKind kind, const void* src_, 
 
 }  // namespace
 
-cudaError_t launch_sweep(const LatticeView& v, SweepKind kind, const void* src, void* dst, const TrtParams& p,
-                         int threads, int cells_per_thread, cudaStream_t s) {
+cudaError_t launch_sweep(const LatticeView& v, SweepKind kind, int parity, const void* src, void* dst,
+                         const TrtParams& p, int threads, int cells_per_thread, cudaStream_t s) {
   switch (v.prec) {
-    case kF64: return sweep_typed<double>(v, kind, src, dst, p, threads, cells_per_thread, s);
-    case kF32: return sweep_typed<float>(v, kind, src, dst, p, threads, cells_per_thread, s);
-    case kF16: return sweep_typed<__half>(v, kind, src, dst, p, threads, cells_per_thread, s);
-    case kF64DF: return sweep_typed<f64df>(v, kind, src, dst, p, threads, cells_per_thread, s);
-    case kF32DF: return sweep_typed<f32df>(v, kind, src, dst, p, threads, cells_per_thread, s);
+    case kF64: return sweep_typed<double>(v, kind, parity, src, dst, p, threads, cells_per_thread, s);
+    case kF32: return sweep_typed<float>(v, kind, parity, src, dst, p, threads, cells_per_thread, s);
+    case kF16: return sweep_typed<__half>(v, kind, parity, src, dst, p, threads, cells_per_thread, s);
+    case kF64DF: return sweep_typed<f64df>(v, kind, parity, src, dst, p, threads, cells_per_thread, s);
+    case kF32DF: return sweep_typed<f32df>(v, kind, parity, src, dst, p, threads, cells_per_thread, s);
+    case kF16SR: return sweep_typed<h16sr>(v, kind, parity, src, dst, p, threads, cells_per_thread, s);
   }
   return cudaErrorInvalidValue;
 }

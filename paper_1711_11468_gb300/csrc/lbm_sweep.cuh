@@ -16,6 +16,9 @@
 // parked in its slot.
 #pragma once
 
+#include <type_traits>
+
+#include "lbm_internal.h"
 #include "lbm_model.cuh"
 
 namespace lbm {
@@ -24,6 +27,30 @@ template <typename S>
 using Arith = typename Storage<S>::A;
 template <typename S>
 using RawT = typename Storage<S>::Raw;
+template <typename S>
+using ParamsT = typename Storage<S>::Params;
+
+// TRT constants in the arithmetic type of storage format S (lbm_sweep.cu).
+template <typename S>
+Trt<Arith<S>> trt_as(const TrtParams& p);
+
+// Launch parameters of one sweep of one lattice: the TRT constants plus, for
+// the stochastic format, the lattice's random stream and the sweep counter of
+// this parity.
+template <typename S>
+ParamsT<S> params_as(const TrtParams& p, const LatticeView& v, int parity) {
+  if constexpr (std::is_same<S, h16sr>::value) {
+    TrtSr q;
+    static_cast<Trt<float>&>(q) = trt_as<S>(p);
+    q.seed = v.sr_seed;
+    q.base = 0;
+    q.ctr = v.sweep_ctr;
+    q.parity = parity & 1;
+    return q;
+  } else {
+    return trt_as<S>(p);
+  }
+}
 
 // Wrapped neighbour offsets of one cell of a full array.
 struct Nbr {
@@ -69,7 +96,7 @@ __device__ __forceinline__ void reverse(R (&f)[Q]) {
 template <typename S, bool kHW>
 __device__ __forceinline__ void pull_dense_node(const S* __restrict__ src, S* __restrict__ dst,
                                                 const uint8_t* __restrict__ flags, int x, int y, int z, int n,
-                                                int nx, int ny, int nz, int64_t stride, const Trt<Arith<S>>& p) {
+                                                int nx, int ny, int nz, int64_t stride, const ParamsT<S>& p) {
   const uint8_t fl = flags[n];
   if (fl == kSolidHalfway) return;
   const Nbr nb(x, y, z, nx, ny, nz);
@@ -85,7 +112,7 @@ __device__ __forceinline__ void pull_dense_node(const S* __restrict__ src, S* __
   if (fl == kSolidFullway)
     reverse(f);
   else
-    Storage<S>::relax(f, p);
+    Storage<S>::relax(f, p, (uint32_t)n);
 #pragma unroll
   for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + n, f[i]);
 }
@@ -93,11 +120,11 @@ __device__ __forceinline__ void pull_dense_node(const S* __restrict__ src, S* __
 // Node-local even step; the caller skips nodes that are not fluid.
 template <typename S>
 __device__ __forceinline__ void aa_even_node(S* __restrict__ pdf, int64_t k, int64_t stride,
-                                             const Trt<Arith<S>>& p) {
+                                             const ParamsT<S>& p) {
   RawT<S> f[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) f[i] = Storage<S>::load(dir(pdf, i, stride) + k);
-  Storage<S>::relax(f, p);
+  Storage<S>::relax(f, p, (uint32_t)k);
 #pragma unroll
   for (int i = 0; i < Q; ++i) Storage<S>::store(dir(pdf, opp(i), stride) + k, f[i]);
 }
@@ -106,7 +133,7 @@ __device__ __forceinline__ void aa_even_node(S* __restrict__ pdf, int64_t k, int
 template <typename S, bool kHW>
 __device__ __forceinline__ void aa_odd_dense_node(S* __restrict__ pdf, const uint8_t* __restrict__ flags, int x,
                                                   int y, int z, int n, int nx, int ny, int nz, int64_t stride,
-                                                  const Trt<Arith<S>>& p) {
+                                                  const ParamsT<S>& p) {
   const Nbr nb(x, y, z, nx, ny, nz);
   RawT<S> f[Q];
 #pragma unroll
@@ -117,7 +144,7 @@ __device__ __forceinline__ void aa_odd_dense_node(S* __restrict__ pdf, const uin
     else
       f[i] = Storage<S>::load(dir(pdf, opp(i), stride) + m);
   }
-  Storage<S>::relax(f, p);
+  Storage<S>::relax(f, p, (uint32_t)n);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int m = n + nb.down(i);
@@ -179,19 +206,19 @@ __device__ __forceinline__ void aa_odd_dense_scatter(S* __restrict__ pdf, const 
 template <typename S>
 __device__ __forceinline__ void pull_list_node(const S* __restrict__ src, S* __restrict__ dst,
                                                const uint32_t* __restrict__ link, int64_t k, int64_t stride,
-                                               const Trt<Arith<S>>& p) {
+                                               const ParamsT<S>& p) {
   RawT<S> f[Q];
   f[0] = Storage<S>::load(src + k);
 #pragma unroll
   for (int i = 1; i < Q; ++i) f[i] = Storage<S>::load(src + __ldg(link + (int64_t)(i - 1) * stride + k));
-  Storage<S>::relax(f, p);
+  Storage<S>::relax(f, p, (uint32_t)k);
 #pragma unroll
   for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + k, f[i]);
 }
 
 template <typename S>
 __device__ __forceinline__ void aa_odd_list_node(S* __restrict__ pdf, const uint32_t* __restrict__ link, int64_t k,
-                                                 int64_t stride, const Trt<Arith<S>>& p) {
+                                                 int64_t stride, const ParamsT<S>& p) {
   uint32_t off[Q];
 #pragma unroll
   for (int i = 1; i < Q; ++i) off[i] = __ldg(link + (int64_t)(i - 1) * stride + k);
@@ -199,7 +226,7 @@ __device__ __forceinline__ void aa_odd_list_node(S* __restrict__ pdf, const uint
   f[0] = Storage<S>::load(pdf + k);
 #pragma unroll
   for (int i = 1; i < Q; ++i) f[i] = Storage<S>::load(pdf + off[i]);
-  Storage<S>::relax(f, p);
+  Storage<S>::relax(f, p, (uint32_t)k);
   Storage<S>::store(pdf + k, f[0]);
   // f*_i goes where f_opp(i) came from: the downstream node's slot i, or slot opp(i) of k
 #pragma unroll
@@ -229,24 +256,24 @@ __device__ __forceinline__ void list_aa_scatter(S* __restrict__ pdf, const uint3
 template <typename S>
 __device__ __forceinline__ void pull_list_node_staged(const S* __restrict__ src, S* __restrict__ dst,
                                                       const uint32_t* slink, int T, int j, int64_t k, int64_t stride,
-                                                      const Trt<Arith<S>>& p) {
+                                                      const ParamsT<S>& p) {
   RawT<S> f[Q];
   f[0] = Storage<S>::load(src + k);
 #pragma unroll
   for (int i = 1; i < Q; ++i) f[i] = Storage<S>::load(src + slink[(i - 1) * T + j]);
-  Storage<S>::relax(f, p);
+  Storage<S>::relax(f, p, (uint32_t)k);
 #pragma unroll
   for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + k, f[i]);
 }
 
 template <typename S>
 __device__ __forceinline__ void aa_odd_list_node_staged(S* __restrict__ pdf, const uint32_t* slink, int T, int j,
-                                                        int64_t k, const Trt<Arith<S>>& p) {
+                                                        int64_t k, const ParamsT<S>& p) {
   RawT<S> f[Q];
   f[0] = Storage<S>::load(pdf + k);
 #pragma unroll
   for (int i = 1; i < Q; ++i) f[i] = Storage<S>::load(pdf + slink[(i - 1) * T + j]);
-  Storage<S>::relax(f, p);
+  Storage<S>::relax(f, p, (uint32_t)k);
   Storage<S>::store(pdf + k, f[0]);
 #pragma unroll
   for (int i = 1; i < Q; ++i) {

@@ -15,12 +15,13 @@ import os
 import numpy as np
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_STATE, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_UNSUPPORTED, LBM_ERR_TIMEOUT = range(7)
-LBM_F64, LBM_F32_SHIFTED, LBM_F16_SHIFTED, LBM_F64_DOUBLE_FLOAT, LBM_F32_SHIFTED_DOUBLE_FLOAT = 0, 1, 2, 3, 4
+(LBM_F64, LBM_F32_SHIFTED, LBM_F16_SHIFTED, LBM_F64_DOUBLE_FLOAT, LBM_F32_SHIFTED_DOUBLE_FLOAT,
+ LBM_F16_SHIFTED_STOCHASTIC) = range(6)
 LBM_DIRECT, LBM_INDIRECT = 0, 1
 LBM_PULL_TWO_GRID, LBM_AA_INPLACE = 0, 1
 
 PRECISION = {"f64": LBM_F64, "f32": LBM_F32_SHIFTED, "f16": LBM_F16_SHIFTED, "f64df": LBM_F64_DOUBLE_FLOAT,
-             "f32df": LBM_F32_SHIFTED_DOUBLE_FLOAT}
+             "f32df": LBM_F32_SHIFTED_DOUBLE_FLOAT, "f16sr": LBM_F16_SHIFTED_STOCHASTIC}
 Q = 19
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblbm_gb300.so")
@@ -79,6 +80,7 @@ def load(path: str | None = None):
         "lbm_init_equilibrium": [H, i32, vp, vp],
         "lbm_step": [H, i32],
         "lbm_synchronize": [H],
+        "lbm_set_stochastic_rounding": [H, ctypes.c_uint64, i64],
         "lbm_steps_done": [H, ctypes.POINTER(i64)],
         "lbm_read_pdfs": [H, i32, vp, sz],
         "lbm_write_pdfs": [H, i32, vp, sz],
@@ -227,6 +229,10 @@ def lbm_init_equilibrium(h: Handle, lattice: int, rho=None, u=None):
 
 def lbm_step(h: Handle, n: int):
     _check(load().lbm_step(h, int(n)))
+
+
+def lbm_set_stochastic_rounding(h: Handle, seed: int, sweep: int = 0):
+    _check(load().lbm_set_stochastic_rounding(h, int(seed) & (2 ** 64 - 1), int(sweep)))
 
 
 def lbm_synchronize(h: Handle):

@@ -26,8 +26,10 @@ pytestmark = pytest.mark.gpu
 # fall below its resolution), so its bound only asks for a finite result.
 # FP32 storage with the double-float collision meets the 1e-5 target: the
 # stored values are rounded once per step, without the correlated rounding of
-# FP32 arithmetic.
-BOUNDS = {0: 1e-9, 3: 1e-9, 1: 1e-4, 2: 1.5, 4: 1e-5}
+# FP32 arithmetic. FP16 storage with stochastic rounding keeps the increments
+# on average; what is left is the noise of the random rounding, averaged over
+# the 384^2 cells of a plane: 4.2e-5, as close as FP32 storage gets.
+BOUNDS = {0: 1e-9, 3: 1e-9, 1: 1e-4, 2: 1.5, 4: 1e-5, 5: 1e-4}
 
 
 def series(y, t, F, nu, a, b, nterms=4001):
@@ -57,7 +59,7 @@ def reference(orc):
 REPORT = {}
 
 
-@pytest.mark.parametrize("prec", [1, 4, 2, 3, 0])
+@pytest.mark.parametrize("prec", [1, 4, 2, 5, 3, 0])
 def test_channel384_profile_error(lbm, reference, prec):
     import torch
     c = inputs.CHANNEL_384
@@ -85,7 +87,7 @@ def test_channel384_profile_error(lbm, reference, prec):
         "mass_rel_drift": float(abs(mass - np.prod(dims)) / np.prod(dims)),
     }
     name = {0: "f64", 1: "f32_shifted", 2: "f16_shifted", 3: "f64_double_float",
-            4: "f32_shifted_double_float"}[prec]
+            4: "f32_shifted_double_float", 5: "f16_shifted_stochastic"}[prec]
     REPORT[name] = err
     path = os.environ.get("LBM_ACCURACY_REPORT")
     if path:
