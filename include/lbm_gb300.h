@@ -82,23 +82,25 @@ typedef enum {
  *                        once when stored: FP32 bytes, with the accuracy that
  *                        FP32 collision arithmetic loses.
  *   LBM_F16_SHIFTED_STOCHASTIC
- *                        f_i - w_i in FP16, FP32 collision, rounded to FP16
- *                        stochastically: up (away from zero) with the
- *                        probability of the remainder, from 16 random bits per
- *                        value. Round-to-nearest FP16 loses every per-step
- *                        change below half an FP16 spacing (a slow forced flow
- *                        stagnates); stochastic rounding keeps them on average.
- *                        The bits come from a counter-based splitmix64 (Steele,
- *                        Lea and Flood, OOPSLA 2014): node k (the cell index, or
- *                        the list index under indirect addressing) at sweep t
- *                        draws key K = output number (t << 32) | k of the stream
- *                        seeded with the lattice's seed, then outputs 0..3 of the
- *                        stream seeded with K; with W_0 = K and W_m those
- *                        outputs, direction j uses bits 16 (j mod 4) .. +15 of
- *                        W_(j div 4) as r, and rounds away from zero iff the
- *                        remainder of |x| past the FP16 value below it, in FP16
- *                        spacings, plus r / 2^16 reaches 1. Finite values beyond
- *                        65504 saturate. Results do not depend on the launch
+ *                        2^14 (f_i - w_i) in FP16, FP32 collision, rounded to
+ *                        FP16 stochastically. Round-to-nearest FP16 loses every
+ *                        per-step change below half an FP16 spacing (a slow
+ *                        forced flow stagnates); stochastic rounding keeps them
+ *                        on average. The scale puts |f_i - w_i| from 2^-28 to 4
+ *                        in FP16's normal range (larger values saturate), where
+ *                        the rounding is: add 13 random bits r to the bit
+ *                        pattern of the FP32 value and truncate to FP16, i.e.
+ *                        round away from zero with probability equal to the
+ *                        remainder over the FP16 spacing, exactly. The bits come
+ *                        from a counter-based splitmix64 (Steele, Lea and Flood,
+ *                        OOPSLA 2014): node k (the cell index, or the list index
+ *                        under indirect addressing) at sweep t draws key
+ *                        K = output number (t << 32) | k of the stream seeded
+ *                        with the lattice's seed, then outputs 0..3 of the stream
+ *                        seeded with K; with W_0 = K and W_m those outputs,
+ *                        direction j reads the 32-bit half (j mod 4) div 2 of
+ *                        W_(j div 4) (0 = low) and takes its bits 0..12 for even
+ *                        j, 19..31 for odd j. Results do not depend on the launch
  *                        shape, the propagation pattern or graph replay. The seed
  *                        and the sweep number are set by
  *                        lbm_set_stochastic_rounding. */

@@ -22,9 +22,10 @@ Parity status of each function (the pins live in ``tests/test_oracle_*.py``):
   macroscopic               pinned (analytic Poiseuille profile)
   splitmix64 / sr_bits      pinned (published splitmix64 outputs; an independent
                             numpy splitmix64; the documented bit layout)
-  round_half_stochastic     pinned (FP16 neighbours from numpy, fixed points,
-                            exact mean over all 2^16 draws, odd symmetry,
-                            subnormal spacing, saturation)
+  round_half_stochastic     pinned (FP16 neighbours from numpy, the FP32 bit
+                            addition it restates, fixed points, exact mean over
+                            all 2^13 draws, odd symmetry, subnormal spacing,
+                            saturation)
   step_f16_stochastic       pinned (every slot is an FP16 neighbour of the FP64
                             step's value; seed-averaged mass and momentum match
                             the FP64 step; full-way reversal is exact)
@@ -243,13 +244,16 @@ def splitmix64(seed: int, k: int) -> int:
     return int(_load().orc_splitmix64(seed & (2 ** 64 - 1), k & (2 ** 64 - 1)))
 
 
+SR_SCALE_LOG2 = 14   # the FP16 stochastic format stores d * 2^14
+
+
 def sr_bits(seed: int, t: int, node: int, j: int) -> int:
-    """The 16 random bits of direction j of node `node` at sweep t (FP16 stochastic format)."""
+    """The 13 random bits of direction j of node `node` at sweep t (FP16 stochastic format)."""
     return int(_load().orc_sr_bits(seed & (2 ** 64 - 1), t, node, j))
 
 
 def round_half_stochastic(x, r):
-    """Stochastic rounding to FP16 of x with random bits r (arrays broadcast):
+    """Stochastic rounding to FP16 of x with 13 random bits r (arrays broadcast):
     returns (values as float64, margins in FP16 spacings)."""
     x, r = np.broadcast_arrays(np.asarray(x, dtype=np.float64), np.asarray(r, dtype=np.uint32))
     x = np.ascontiguousarray(x)
@@ -262,8 +266,8 @@ def round_half_stochastic(x, r):
 
 
 def step_f16_stochastic(dims, flags, omega_plus, omega_minus_, F, d_src, seed: int, t: int, node_of=None):
-    """One push step of the FP16-shifted stochastic format on deviations d = f - w:
-    returns (d(t+1) [19, N], margin [19, N])."""
+    """One push step of the scaled FP16-shifted stochastic format on deviations
+    d = f - w (FP16 values times 2^-14): returns (d(t+1) [19, N], margin [19, N])."""
     nx, ny, nz = dims
     flags = _u8(flags)
     d_src = _f64(d_src)

@@ -266,27 +266,34 @@ uint32_t orc_sr_bits(uint64_t seed, uint64_t t, uint64_t node, int j) {
   uint64_t key = orc_splitmix64(seed, (t << 32) | node);
   int m = j / 4;
   uint64_t word = m == 0 ? key : orc_splitmix64(key, (uint64_t)(m - 1));
-  return (uint32_t)((word >> (16 * (j % 4))) & 0xFFFFu);
+  uint32_t half = (uint32_t)(((j % 4) / 2) == 0 ? word : word >> 32);
+  return (j % 2) == 0 ? (half & 0x1FFFu) : (half >> 19);
 }
 
-/* Stochastic rounding to FP16 (see the header). Every step is exact in FP64:
- * u is a power of two, |x| / u has at most 53 significant bits, and
- * q + r / 2^16 keeps them (q < 1, r / 2^16 has 16 fraction bits). */
+/* Stochastic rounding to FP16 (see the header). u and v are powers of two and
+ * a / u is exact. In FP16's normal range r v / u = r / 2^13 and q + r / 2^13
+ * is exact too; below it the sum is exact except for a in [2^-25, 2^-24),
+ * where it may round in its last bit (q and r v / u span 54 bits there). */
 double orc_round_half_stochastic(double x, uint32_t r, double* margin) {
   if (isnan(x) || isinf(x)) {
     if (margin) *margin = INFINITY;
     return x;
   }
   double a = fabs(x);
+  if (a == 0.0) {
+    if (margin) *margin = INFINITY;
+    return x;
+  }
   int e;
-  (void)frexp(a, &e);          /* a = m * 2^e with m in [0.5, 1): a in [2^(e-1), 2^e) */
-  int ue = (e - 1) - 10;       /* FP16 spacing for a in [2^(e-1), 2^e) */
-  if (a == 0.0 || ue < -24) ue = -24;
+  (void)frexp(a, &e);   /* a = m * 2^e, m in [0.5, 1): a in [2^(e-1), 2^e) */
+  int ex = e - 1;       /* a in [2^ex, 2^(ex+1)) */
+  int ve = ex < -126 ? -149 : ex - 23;
+  int ue = ex < -14 ? -24 : ex - 10;
   double u = ldexp(1.0, ue);
   double s = a / u;
   double lo = floor(s);
   double q = s - lo;
-  double up = q + (double)r / 65536.0;
+  double up = q + (double)r * ldexp(1.0, ve - ue);
   double res;
   if (q == 0.0) {
     res = lo * u;
@@ -324,8 +331,11 @@ void orc_step_f16_stochastic(int nx, int ny, int nz, const uint8_t* flags, doubl
           for (int i = 0; i < ORC_Q; ++i) f[i] = orc_weight(i) + d_src[(size_t)i * N + n];
           orc_collide_trt(f, omega_plus, omega_minus, F, fs);
           uint64_t node = node_of ? (uint64_t)node_of[n] : (uint64_t)n;
-          for (int i = 0; i < ORC_Q; ++i)
-            ds[i] = orc_round_half_stochastic(fs[i] - orc_weight(i), orc_sr_bits(seed, t, node, i), &mg[i]);
+          for (int i = 0; i < ORC_Q; ++i) {
+            double x = ldexp(fs[i] - orc_weight(i), ORC_F16_SCALE_LOG2);
+            ds[i] = ldexp(orc_round_half_stochastic(x, orc_sr_bits(seed, t, node, i), &mg[i]),
+                          -ORC_F16_SCALE_LOG2);
+          }
         }
         for (int i = 0; i < ORC_Q; ++i) {
           int dx = wrap(x + CX[i], nx), dy = wrap(y + CY[i], ny), dz = wrap(z + CZ[i], nz);

@@ -82,46 +82,57 @@ void orc_macroscopic(int nx, int ny, int nz, const uint8_t* flags, const double 
                      const double* f, double* rho, double* u);
 
 /* ---------------------------------------------------------------------------
- * FP16-shifted storage with stochastic rounding (an accuracy remedy for the
- * FP16-shifted format; not in the paper, whose error study of reduced
+ * Scaled FP16-shifted storage with stochastic rounding (an accuracy remedy for
+ * the FP16-shifted format; not in the paper, whose error study of reduced
  * precision storage is the verification set-up of Sec. 2.1).
  *
- * State: deviations d_i = f_i - w_i, each an FP16 value held in a double.
- * One step: f = w + d, the FP64 collision and bounce-back of orc_step, then
- * each post-collision deviation f*_j - w_j of a fluid node is rounded to FP16
- * stochastically with 16 random bits r(seed, t, node, j); full-way solid
- * nodes only reverse their (already FP16) values.
+ * State: deviations d_i = f_i - w_i, stored as the FP16 value h_i of
+ * d_i * 2^14 (so FP16's normal range covers |d| from 2^-28 to 4); held here as
+ * doubles d_i = h_i * 2^-14. One step: f = w + d, the FP64 collision and
+ * bounce-back of orc_step, then each post-collision value x = (f*_j - w_j) 2^14
+ * of a fluid node is rounded to FP16 stochastically with 13 random bits
+ * r(seed, t, node, j); full-way solid nodes only reverse their (already FP16)
+ * values.
  *
  * Random bits (counter-based, splitmix64 of Steele, Lea and Flood, OOPSLA
  * 2014): node `node` at sweep t draws the key
  *   K = splitmix64 output number ((t << 32) | node) of the stream seeded `seed`,
  * then the words W_0 = K and W_m = output number m-1 of the stream seeded K
- * (m = 1..4); direction j takes bits 16*(j mod 4) .. +15 of W_(j div 4).
+ * (m = 1..4). Direction j reads the 32-bit half (j mod 4) div 2 of
+ * W_(j div 4) (0 = low) and takes its bits 0..12 for even j, 19..31 for odd j.
  *
- * Rounding rule: with u = the FP16 spacing at |x| (2^(e-10) for |x| in
- * [2^e, 2^(e+1)), e >= -14; 2^-24 below 2^-14), lo = u * floor(|x| / u) and
- * q = |x| / u - floor(|x| / u), the result is sign(x) * (lo + u) if
- * q + r / 2^16 >= 1, else sign(x) * lo; finite results saturate at 65504.
- * Averaged over the 2^16 values of r this is |x| to within u / 2^16.
+ * Rounding rule (the addition of r to the magnitude bits of an FP32 number,
+ * then truncation to FP16): with a = |x|, v = 2^(e-23) the FP32 spacing at a
+ * (a in [2^e, 2^(e+1)); 2^-149 below 2^-126), u the FP16 spacing at a
+ * (2^(e-10) for e >= -14, 2^-24 below), lo = u floor(a / u), the result is
+ * sign(x) (lo + u) if a + r v >= lo + u, else sign(x) lo; finite results
+ * saturate at 65504. For a in FP16's normal range, v = u / 2^13: an FP32 value
+ * a rounds away from zero with probability exactly (a - lo) / u (unbiased).
+ * Below 2^-14 the added amount is smaller than u, so there the rounding leans
+ * towards zero (scaled, this is |d| < 2^-28).
  * ------------------------------------------------------------------------ */
+
+/* log2 of the storage scale of the format: d * 2^14 is stored. */
+#define ORC_F16_SCALE_LOG2 14
 
 /* Output number k (0-based) of splitmix64 seeded `seed`: mix(seed + (k+1) * gamma). */
 uint64_t orc_splitmix64(uint64_t seed, uint64_t k);
 
-/* The 16 random bits of direction j of node `node` at sweep t. */
+/* The 13 random bits of direction j of node `node` at sweep t. */
 uint32_t orc_sr_bits(uint64_t seed, uint64_t t, uint64_t node, int j);
 
-/* Stochastic rounding of x to FP16 with random bits r (0..65535). If margin
- * is not NULL it receives |q + r/2^16 - 1|, the distance of the decision from
- * its threshold in units of the FP16 spacing (infinite when x is an FP16 value). */
+/* Stochastic rounding of x to FP16 with random bits r (0..8191), the rule
+ * above. If margin is not NULL it receives |(a + r v - lo - u) / u|, the
+ * distance of the decision from its threshold in FP16 spacings (infinite when
+ * x is an FP16 value). */
 double orc_round_half_stochastic(double x, uint32_t r, double* margin);
 
 /* The same over arrays: out[k] and margin[k] (margin may be NULL) for x[k], r[k]. */
 void orc_round_half_stochastic_n(const double* x, const uint32_t* r, int64_t n, double* out, double* margin);
 
-/* One push step of the FP16-shifted stochastic format: d_src holds the
- * deviations at sweep t (0 at half-way solid cells), d_dst receives them at
- * t+1 (must be zero at half-way solid cells on entry). node_of[N] numbers the
+/* One push step of the format: d_src holds the deviations at sweep t (FP16
+ * values times 2^-14; 0 at half-way solid cells), d_dst receives them at t+1
+ * (must be zero at half-way solid cells on entry). node_of[N] numbers the
  * nodes that draw the random bits (NULL: the cell index). margin (NULL, or
  * double[19][N]) receives, for each slot of d_dst, the margin of the rounding
  * that produced it (INFINITY where no rounding happened). */

@@ -94,7 +94,12 @@ struct TrtSr : Trt<float> {
 // the same pairwise algebra with rho replaced by drho in the constant term.
 // With the increment constants (a - 1/2, b - 1/2, rest - 1) the same code
 // returns f*_i - f_i instead of f*_i.
-template <typename A, bool kShifted>
+// With kScaled, f holds 2^14 d_i (the scaled stochastic FP16 format): the
+// collision of scaled values is the same code with rho = 1 + 2^-14 rho0, the
+// 3/2 of the u.u term and c4 divided by 2^14 and the force terms multiplied by
+// 2^14 (the constants in p carry the latter two). Powers of two scale exactly,
+// so this computes 2^14 times what the unscaled FP32 collision computes.
+template <typename A, bool kShifted, bool kScaled = false>
 __device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
   A s[10], d[10];
 #pragma unroll
@@ -103,7 +108,8 @@ __device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
     d[k] = f[k] - f[k + 9];
   }
   const A rho0 = f[0] + (((s[1] + s[2]) + (s[3] + s[4])) + ((s[5] + s[6]) + (s[7] + s[8])) + s[9]);
-  const A rho = kShifted ? A(1.0f) + rho0 : rho0;
+  constexpr float kInvScale = 1.0f / (float)(1 << kSrScaleLog2);
+  const A rho = kShifted ? (kScaled ? rho0 * A(kInvScale) + A(1.0f) : A(1.0f) + rho0) : rho0;
   const A jx = (d[1] + d[4]) + (d[5] + d[6]) + d[7];
   const A jy = (d[2] + d[4]) - d[5] + (d[8] + d[9]);
   const A jz = (d[3] + d[6]) - d[7] + (d[8] - d[9]);
@@ -111,7 +117,7 @@ __device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
   const A ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
   const A usq = ux * ux + uy * uy + uz * uz;
   // constant part of e+ per unit weight: rho0 - 3/2 rho u.u
-  const A base = rho0 - A(1.5f) * (rho * usq);
+  const A base = rho0 - A(kScaled ? 1.5f * kInvScale : 1.5f) * (rho * usq);
   const A bw[2] = {p.wp_w[0] * base, p.wp_w[1] * base};   // w+ w_c base
 
   f[0] = p.rest * f[0] + p.wp_w0 * base;
@@ -142,7 +148,7 @@ __device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
 //            once on store. FP32 collision arithmetic makes correlated
 //            rounding errors that accumulate over steps; rounding a precisely
 //            collided value only at the store does not.
-//   h16sr  : d_i = f_i - w_i in FP16, collided in FP32, rounded to FP16
+//   h16sr  : 2^14 d_i in FP16, collided in FP32 (scaled), rounded to FP16
 //            stochastically (lbm_sr.cuh) with the random bits of the node.
 //            Raw values are the FP16 bit patterns, so that moving them (and
 //            reversing them at full-way solids) needs no conversion.
@@ -262,7 +268,7 @@ struct Storage<f32df> {
 
 template <>
 struct Storage<h16sr> {
-  using Raw = uint32_t;   // the FP16 bit pattern in the low half
+  using Raw = uint32_t;   // the FP16 bit pattern in the low half; the high half is ignored
   using A = float;
   using Params = TrtSr;
   static constexpr bool kShifted = true, kIncrement = false;
@@ -276,14 +282,18 @@ struct Storage<h16sr> {
     float d[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = __half2float(__ushort_as_half((unsigned short)f[i]));
-    collide<float, true>(d, p);
+    collide<float, true, true>(d, p);
     unsigned long long w[5];
     sr_words(p.base, node, w);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = round_half_stochastic(d[i], sr_fraction(w, i));
+    for (int i = 0; i < Q; ++i) f[i] = round_half_stochastic(d[i], sr_bits(w, i));
   }
-  __device__ __forceinline__ static double to_f64(h16sr v, int i) { return weight(i) + (double)__half2float(v.v); }
-  __device__ __forceinline__ static h16sr from_f64(double f, int i) { return h16sr{__double2half(f - weight(i))}; }
+  __device__ __forceinline__ static double to_f64(h16sr v, int i) {
+    return weight(i) + ldexp((double)__half2float(v.v), -kSrScaleLog2);
+  }
+  __device__ __forceinline__ static h16sr from_f64(double f, int i) {
+    return h16sr{__double2half(ldexp(f - weight(i), kSrScaleLog2))};
+  }
 };
 
 // Per-sweep set-up of the launch parameters. Every thread of the launch calls

@@ -1,16 +1,26 @@
-// Stochastic rounding of FP16-shifted storage. Round-to-nearest FP16 storage
-// stagnates when the per-step change of a deviation d_i = f_i - w_i is below
-// half its FP16 spacing (a slow body-force flow: 3 w_i c_i.F ~ 2e-8 against a
-// spacing of 6e-8 near 1e-4). Rounding up with the probability of the
-// remainder keeps every stored value unbiased, so the small increments survive
-// on average.
+// Stochastic rounding of scaled FP16-shifted storage. Round-to-nearest FP16
+// storage stagnates when the per-step change of a deviation d_i = f_i - w_i is
+// below half its FP16 spacing (a slow body-force flow: 3 w_i c_i.F ~ 2e-8
+// against a spacing of 6e-8 near 1e-4). Rounding up with the probability of
+// the remainder keeps every stored value unbiased, so the small increments
+// survive on average.
+//
+// The format stores d_i 2^14 (kSrScaleLog2): FP16's normal range then covers
+// |d| from 2^-28 to 4, and for a number in that range stochastic rounding of an
+// FP32 value is one integer addition: add 13 random bits to its bit pattern
+// (the 13 bits FP32 keeps below the FP16 spacing) and truncate to FP16. The
+// result is the FP16 neighbour away from zero exactly when the 13 dropped bits
+// plus the draw carry, i.e. with probability (remainder / spacing), without
+// bias. Below 2^-14 (scaled) the addition covers less than one FP16 spacing and
+// the rounding leans towards zero; those values are below 2^-28 unscaled.
 //
 // Random bits: splitmix64 (Steele, Lea and Flood, "Fast splittable
 // pseudorandom number generators", OOPSLA 2014) used as a counter-based
 // generator. Node `node` at sweep t draws its key, output number
 // (t << 32) | node of the stream seeded with the lattice's seed, and four more
-// words, outputs 0..3 of the stream the key seeds; direction j takes bits
-// 16 (j mod 4) .. +15 of word j div 4.
+// words, outputs 0..3 of the stream the key seeds; direction j reads the 32-bit
+// half (j mod 4) div 2 of word j div 4 and takes its bits 0..12 (even j) or
+// 19..31 (odd j).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -35,24 +45,20 @@ __device__ __forceinline__ void sr_words(unsigned long long base, uint32_t node,
   for (int m = 1; m < 5; ++m) w[m] = splitmix_mix(w[0] + (unsigned long long)m * kSplitmixGamma);
 }
 
-// r / 2^16 as an FP32 value, for the 16 random bits of direction j.
-__device__ __forceinline__ float sr_fraction(const unsigned long long (&w)[5], int j) {
-  const unsigned word = (j % 4) < 2 ? (unsigned)w[j / 4] : (unsigned)(w[j / 4] >> 32);
-  const unsigned bits = (j % 2) == 0 ? (word << 7) & 0x007FFF80u : (word >> 9) & 0x007FFF80u;
-  return __uint_as_float(0x3F800000u | bits) - 1.0f;   // 1 + r 2^-16 is exact, and so is the subtraction
+constexpr int kSrScaleLog2 = 14;
+
+// The 13 random bits of direction j.
+__device__ __forceinline__ unsigned sr_bits(const unsigned long long (&w)[5], int j) {
+  const unsigned half = (j % 4) < 2 ? (unsigned)w[j / 4] : (unsigned)(w[j / 4] >> 32);
+  return (j % 2) == 0 ? (half & 0x1FFFu) : (half >> 19);
 }
 
-// FP32 -> FP16 bits with stochastic rounding: with u the FP16 spacing at |x|,
-// the result is the FP16 neighbour of x away from zero if the remainder of |x|
-// past the one towards zero plus r u reaches u, else that one. The fused
-// multiply-add rounds towards zero, so |x| + r u stays below the next FP16 value
-// exactly when the exact sum does: the decision is exact for the FP32 input.
-// Finite values beyond the FP16 range saturate at 65504.
-__device__ __forceinline__ unsigned short round_half_stochastic(float x, float r) {
-  const unsigned e = __float_as_uint(x) & 0x7F800000u;
-  const float u = __uint_as_float(max(e, 0x38800000u) - (10u << 23));   // 2^(max(e, -14) - 10)
-  const float y = __fmaf_rz(r, u, fabsf(x));
-  return __half_as_ushort(__float2half_rz(copysignf(y, x)));
+// FP32 -> FP16 bits, stochastically: the draw is added to the magnitude bits
+// (a carry out of the mantissa moves to the next binade, which is the value
+// the rounding goes up to), then the conversion truncates. Infinities may turn
+// into NaN; finite values beyond the FP16 range saturate at 65504.
+__device__ __forceinline__ unsigned short round_half_stochastic(float x, unsigned r13) {
+  return __half_as_ushort(__float2half_rz(__uint_as_float(__float_as_uint(x) + r13)));
 }
 
 }  // namespace lbm

@@ -192,14 +192,14 @@ struct PairIO<float> {
   }
 };
 template <>
-struct PairIO<h16sr> {   // raw values are the bit patterns: no conversion
+struct PairIO<h16sr> {   // raw values are the bit patterns in the low halves: no conversion, no masking
   __device__ __forceinline__ static void load(const h16sr* p, uint32_t& a, uint32_t& b) {
     const unsigned u = __ldcs(reinterpret_cast<const unsigned*>(p));
-    a = u & 0xFFFFu;
+    a = u;
     b = u >> 16;
   }
   __device__ __forceinline__ static void store(h16sr* p, uint32_t a, uint32_t b) {
-    __stcs(reinterpret_cast<unsigned*>(p), a | (b << 16));
+    __stcs(reinterpret_cast<unsigned*>(p), __byte_perm(a, b, 0x5410u));
   }
 };
 template <>

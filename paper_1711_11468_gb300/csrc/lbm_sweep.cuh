@@ -42,6 +42,10 @@ ParamsT<S> params_as(const TrtParams& p, const LatticeView& v, int parity) {
   if constexpr (std::is_same<S, h16sr>::value) {
     TrtSr q;
     static_cast<Trt<float>&>(q) = trt_as<S>(p);
+    // the collision of scaled values (see collide): c4 / 2^14, force terms * 2^14
+    const float scale = (float)(1 << kSrScaleLog2);
+    for (int c = 0; c < 2; ++c) q.c4[c] /= scale;
+    for (int k = 0; k < 9; ++k) q.fk[k] = (float)(p.fk[k] * (double)scale);
     q.seed = v.sr_seed;
     q.base = 0;
     q.ctr = v.sweep_ctr;

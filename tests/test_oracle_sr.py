@@ -1,11 +1,14 @@
-"""Pins of the oracle's FP16 stochastic-rounding format: the counter-based
-generator against its published outputs and an independent implementation,
-the rounding rule against numpy's FP16 grid and its exact mean, and the step
-against the FP64 step it rounds. No GPU."""
+"""Pins of the oracle's scaled FP16 stochastic-rounding format: the
+counter-based generator against its published outputs and an independent
+implementation, the rounding rule against numpy's FP16 grid, against the FP32
+bit addition it restates and against its exact mean, and the step against the
+FP64 step it rounds. No GPU."""
 import numpy as np
 import pytest
 
 from paper_1711_11468_gb300 import inputs
+
+SCALE = 2.0 ** 14   # the format stores d * 2^14
 
 
 def fp16_neighbours(x):
@@ -18,8 +21,26 @@ def fp16_neighbours(x):
     return lo.astype(np.float64), hi.astype(np.float64)
 
 
+def scaled_neighbours(d):
+    """Neighbours of deviations d on the format's grid (FP16 values times 2^-14)."""
+    lo, hi = fp16_neighbours(np.asarray(d, dtype=np.float64) * SCALE)
+    return lo / SCALE, hi / SCALE
+
+
 def random_magnitudes(rng, n, lo_exp=-30, hi_exp=15):
     return np.exp2(rng.uniform(lo_exp, hi_exp, n)) * rng.choice([-1.0, 1.0], n)
+
+
+def bit_add_then_truncate(x32, r):
+    """The mechanism the rule restates, written with numpy: add r to the bits
+    of the FP32 number, then truncate the result towards zero to FP16."""
+    y = (x32.view(np.uint32) + np.asarray(r, dtype=np.uint32)).view(np.float32).astype(np.float64)
+    with np.errstate(over="ignore"):
+        c = y.astype(np.float16)
+    c64 = c.astype(np.float64)
+    over = np.abs(c64) > np.abs(y)
+    c = np.where(over, np.nextafter(c, np.float16(0)), c)
+    return np.clip(c.astype(np.float64), -65504.0, 65504.0)
 
 
 # ------------------------------------------------------------- generator
@@ -41,8 +62,9 @@ def test_splitmix64_matches_independent_numpy(orc):
 
 
 def test_sr_bits_layout(orc):
-    """Direction j of node n at sweep t: bits 16 (j mod 4) of word j div 4, where
-    word 0 is the node's key and words 1..4 continue the stream the key seeds."""
+    """Direction j of node n at sweep t: the 32-bit half (j mod 4) div 2 of word
+    j div 4, bits 0..12 for even j and 19..31 for odd j, where word 0 is the
+    node's key and words 1..4 continue the stream the key seeds."""
     rng = np.random.default_rng(11)
     for _ in range(40):
         seed = int(rng.integers(0, 2 ** 63)) * 2 + int(rng.integers(0, 2))
@@ -51,81 +73,105 @@ def test_sr_bits_layout(orc):
         key = int(inputs.splitmix64(np.array([(t << 32) | node], dtype=np.uint64), seed)[0])
         words = [key] + [int(v) for v in inputs.splitmix64(np.arange(4, dtype=np.uint64), key)]
         for j in range(19):
-            assert orc.sr_bits(seed, t, node, j) == (words[j // 4] >> (16 * (j % 4))) & 0xFFFF
+            half = (words[j // 4] >> (32 * ((j % 4) // 2))) & 0xFFFFFFFF
+            want = half & 0x1FFF if j % 2 == 0 else half >> 19
+            assert orc.sr_bits(seed, t, node, j) == want
 
 
 def test_sr_bits_statistics(orc):
-    """The draws are uniform on 0..65535 and differ between nodes, directions and sweeps."""
-    vals = np.array([orc.sr_bits(5, t, n, j) for t in range(3) for n in range(60) for j in range(19)],
+    """The draws are uniform on 0..8191 and differ between nodes, directions and sweeps."""
+    vals = np.array([orc.sr_bits(5, t, n, j) for t in range(3) for n in range(80) for j in range(19)],
                     dtype=np.float64)
-    assert vals.min() >= 0 and vals.max() <= 65535
-    assert abs(vals.mean() / 65536 - 0.5) < 0.02
-    assert abs(vals.std() / 65536 - np.sqrt(1 / 12)) < 0.02
-    assert len(np.unique(vals)) > 0.95 * len(vals)
-    assert orc.sr_bits(5, 0, 0, 0) != orc.sr_bits(6, 0, 0, 0)
+    assert vals.min() >= 0 and vals.max() <= 8191
+    assert abs(vals.mean() / 8192 - 0.5) < 0.02
+    assert abs(vals.std() / 8192 - np.sqrt(1 / 12)) < 0.02
+    counts = np.bincount((vals // 512).astype(int), minlength=16)
+    expect = vals.size / 16
+    assert ((counts - expect) ** 2 / expect).sum() < 40   # chi-square, 15 degrees of freedom
+    assert [orc.sr_bits(5, 0, 0, j) for j in range(19)] != [orc.sr_bits(6, 0, 0, j) for j in range(19)]
 
 
 # ---------------------------------------------------------- rounding rule
 def test_round_half_gives_a_neighbour(orc):
     rng = np.random.default_rng(3)
     x = random_magnitudes(rng, 20000)
-    r = rng.integers(0, 65536, x.size)
+    r = rng.integers(0, 8192, x.size)
     got, margin = orc.round_half_stochastic(x, r)
     lo, hi = fp16_neighbours(x)
-    inside = (np.abs(x) < 65504)
+    inside = np.abs(x) < 65504
     assert np.all((got[inside] == lo[inside]) | (got[inside] == hi[inside]))
-    # the decision: away from zero iff q + r/2^16 >= 1, q the position of |x| between its neighbours
+    # the decision: away from zero iff |x| + r v reaches the neighbour away from zero,
+    # v the FP32 spacing at |x|
+    a = np.abs(x)
+    v = np.exp2(np.floor(np.log2(a)) - 23)
     a_lo = np.minimum(np.abs(lo), np.abs(hi))
     a_hi = np.maximum(np.abs(lo), np.abs(hi))
-    q = (np.abs(x) - a_lo) / (a_hi - a_lo)
     away = np.abs(got) == a_hi
     sel = inside & (a_hi > a_lo)
-    assert np.array_equal(away[sel], (q + r / 65536.0 >= 1.0)[sel])
-    assert np.allclose(margin[sel], np.abs(q + r / 65536.0 - 1.0)[sel], rtol=0, atol=1e-12)
+    assert np.array_equal(away[sel], (a + r * v >= a_hi)[sel])
+    assert np.allclose(margin[sel], (np.abs(a + r * v - a_hi) / (a_hi - a_lo))[sel], rtol=1e-9, atol=1e-12)
+
+
+def test_round_half_is_the_fp32_bit_addition(orc):
+    """For FP32 inputs the rule is: add r to the bit pattern, truncate to FP16."""
+    rng = np.random.default_rng(13)
+    x32 = random_magnitudes(rng, 50000, lo_exp=-40, hi_exp=16).astype(np.float32)
+    x32 = np.concatenate([x32, np.float32([0.0, -0.0, 65504.0, 65519.0, -65535.0, 2.0 ** -24, 2.0 ** -14])])
+    r = rng.integers(0, 8192, x32.size).astype(np.uint32)
+    got, _ = orc.round_half_stochastic(x32.astype(np.float64), r)
+    want = bit_add_then_truncate(x32, r)
+    assert np.array_equal(got, want)
 
 
 def test_round_half_fixed_points(orc):
     """Every finite FP16 value is returned unchanged, whatever the draw."""
     h = np.arange(65536, dtype=np.uint32).astype(np.uint16).view(np.float16)
     h = h[np.isfinite(h)].astype(np.float64)
-    r = np.random.default_rng(0).integers(0, 65536, h.size)
+    r = np.random.default_rng(0).integers(0, 8192, h.size)
     got, margin = orc.round_half_stochastic(h, r)
     assert np.array_equal(got, h)
     assert np.all(np.isinf(margin))
 
 
 def test_round_half_mean_over_all_draws_is_x(orc):
-    """Averaged over all 2^16 draws the rounding returns x to within one
-    2^16-th of the FP16 spacing: the rounding is unbiased."""
+    """Over all 2^13 draws an FP32 value in FP16's normal range rounds away from
+    zero exactly (|x| - lo) / u of the time: the mean is x itself. A general
+    FP64 value is matched to within u / 2^13."""
     rng = np.random.default_rng(5)
-    r = np.arange(65536, dtype=np.uint32)
-    for x in list(random_magnitudes(rng, 12)) + [1.0 / 3.0, -2.0 ** -20 * 1.37, 5e-8, 1e-4 + 1e-9]:
+    r = np.arange(8192, dtype=np.uint32)
+    for x in random_magnitudes(rng, 12, lo_exp=-14, hi_exp=15).astype(np.float32).astype(np.float64):
         got, _ = orc.round_half_stochastic(np.full(r.size, x), r)
         lo, hi = fp16_neighbours(np.array([x]))
-        u = abs(hi[0] - lo[0])
-        assert abs(got.mean() - x) <= u / 65536 + 1e-300, x
+        u = hi[0] - lo[0]
+        if u == 0:
+            continue
+        ups = int(np.count_nonzero(got == hi[0]))
+        assert lo[0] + u * ups / 8192 == x
+    for x in list(random_magnitudes(rng, 12, lo_exp=-14, hi_exp=15)) + [1.0 / 3.0, 1e-4 + 1e-9]:
+        got, _ = orc.round_half_stochastic(np.full(r.size, x), r)
+        lo, hi = fp16_neighbours(np.array([x]))
+        assert abs(got.mean() - x) <= abs(hi[0] - lo[0]) / 8192 * (1 + 1e-12), x
 
 
 def test_round_half_odd_symmetry_and_subnormals(orc):
     rng = np.random.default_rng(9)
     x = random_magnitudes(rng, 5000, lo_exp=-40, hi_exp=-13)
-    r = rng.integers(0, 65536, x.size)
+    r = rng.integers(0, 8192, x.size)
     a, _ = orc.round_half_stochastic(x, r)
     b, _ = orc.round_half_stochastic(-x, r)
     assert np.array_equal(a, -b)
     sub = np.abs(x) < 2.0 ** -14
-    # FP16 subnormal range: results are whole multiples of 2^-24
-    k = a[sub] / 2.0 ** -24
+    k = a[sub] / 2.0 ** -24   # FP16 subnormal range: whole multiples of 2^-24
     assert np.array_equal(k, np.round(k))
-    # below 2^-24 the result is 0 or +-2^-24 with probability |x| / 2^-24
-    tiny = np.full(65536, 0.25 * 2.0 ** -24)
-    got, _ = orc.round_half_stochastic(tiny, np.arange(65536, dtype=np.uint32))
-    assert set(np.unique(got)) == {0.0, 2.0 ** -24}
-    assert (got > 0).sum() == 16384
+    # below 2^-14 the added amount r 2^-38 covers half a spacing: a value 3/4 of the
+    # way to the next grid point rounds up for the draws r >= 2^12 only
+    x0 = (600 + 0.75) * 2.0 ** -24
+    got, _ = orc.round_half_stochastic(np.full(8192, x0), np.arange(8192, dtype=np.uint32))
+    assert (got > 600 * 2.0 ** -24).sum() == 4096
 
 
 def test_round_half_saturation_and_specials(orc):
-    got, _ = orc.round_half_stochastic([70000.0, -1e9, 65519.0, 65503.9], [65535, 65535, 65535, 65535])
+    got, _ = orc.round_half_stochastic([70000.0, -1e9, 65519.0, 65503.9], [8191, 8191, 8191, 8191])
     assert list(got) == [65504.0, -65504.0, 65504.0, 65504.0]
     got, _ = orc.round_half_stochastic([np.inf, -np.inf, np.nan], [0, 0, 0])
     assert got[0] == np.inf and got[1] == -np.inf and np.isnan(got[2])
@@ -133,14 +179,15 @@ def test_round_half_saturation_and_specials(orc):
 
 # ------------------------------------------------------------------ step
 def fp16_state(orc, dims, flags, seed, amp=0.02):
-    """A seeded FP16-grid deviation state: the equilibrium of a random velocity
-    field (density 1 +- 1 %), deviations from w rounded to FP16 by numpy."""
+    """A seeded state on the format's grid: the equilibrium of a random velocity
+    field (density 1 +- 1 %), deviations from w scaled by 2^14 and rounded to
+    FP16 by numpy."""
     nx, ny, nz = dims
     u = inputs.velocity_perturbation(nx, ny, nz, seed=seed, amplitude=amp, flags=flags)
     rho = 1.0 + 0.01 * inputs.uniform_pm1(np.arange(nx * ny * nz, dtype=np.uint64), seed + 1000)
     f = orc.init_equilibrium(dims, flags, rho, u)
     w = orc.weights()[:, None]
-    d = (f - w).astype(np.float16).astype(np.float64)
+    d = ((f - w) * SCALE).astype(np.float16).astype(np.float64) / SCALE
     d[:, flags == 2] = 0.0
     return d
 
@@ -163,7 +210,7 @@ def test_step_f16_stochastic_rounds_the_fp64_step(orc, seed):
     x = ref - w
     got, margin = orc.step_f16_stochastic(dims, fl, om, wm, F, d, seed=0xDEADBEEF + seed, t=77)
     rounded = np.isfinite(margin)
-    lo, hi = fp16_neighbours(x)
+    lo, hi = scaled_neighbours(x)
     assert np.all((got[rounded] == lo[rounded]) | (got[rounded] == hi[rounded]))
     # slots filled by a full-way solid are its own reversed values, untouched
     c = orc.velocities()
@@ -177,7 +224,6 @@ def test_step_f16_stochastic_rounds_the_fp64_step(orc, seed):
             assert got[slot] == d[opp[i], n]
             assert np.isinf(margin[slot])
     assert np.all(got[:, fl == 2] == 0)
-    # a fluid node's slots are all rounded (an FP16-exact value counts as rounded with an infinite margin)
     assert rounded.sum() > 0.5 * rounded.size
     # another sweep counter draws other bits
     got2, _ = orc.step_f16_stochastic(dims, fl, om, wm, F, d, seed=0xDEADBEEF + seed, t=78)
@@ -197,15 +243,12 @@ def test_step_f16_stochastic_is_unbiased(orc):
     x[:, fl == 2] = 0.0   # half-way solid cells hold nothing
     S = 400
     runs = np.stack([orc.step_f16_stochastic(dims, fl, om, wm, F, d, seed=s, t=3)[0] for s in range(S)])
-    lo, hi = fp16_neighbours(x)
+    lo, hi = scaled_neighbours(x)
     u = hi - lo
-    # per slot: the sample mean of a two-point variable lies within 5 sigma of x
-    sigma = 0.5 * u / np.sqrt(S)
-    assert np.all(np.abs(runs.mean(0) - x) <= 5 * sigma + 1e-300)
-    # mass: the seed-averaged total against the FP64 total
+    sigma = 0.5 * u / np.sqrt(S)   # per slot: the sample mean of a two-point variable
+    assert np.all(np.abs(runs.mean(0) - x) <= 5 * sigma + u / 8192 + 1e-300)
     tot = runs.sum(axis=(1, 2))
     assert abs(tot.mean() - x.sum()) <= 5 * tot.std() / np.sqrt(S) + 1e-18
-    # per-seed totals do differ (the draws are live)
     assert tot.std() > 0
 
 
@@ -222,9 +265,8 @@ def test_step_f16_stochastic_node_numbering(orc):
     w = orc.weights()
     for n in (0, 21, 59):
         k = int(list_index[n])
-        f = w + d[:, n]
-        fs = orc.collide_trt(f, om, wm, F)
-        want, _ = orc.round_half_stochastic(fs[0] - w[0], orc.sr_bits(seed, t, k, 0))
-        assert a[0, n] == want[()]
+        fs = orc.collide_trt(w + d[:, n], om, wm, F)
+        want, _ = orc.round_half_stochastic((fs[0] - w[0]) * SCALE, orc.sr_bits(seed, t, k, 0))
+        assert a[0, n] == want[()] / SCALE
     b, _ = orc.step_f16_stochastic(dims, fl, om, wm, F, d, seed=seed, t=t)
     assert not np.array_equal(a, b)
