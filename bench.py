@@ -200,20 +200,42 @@ def make_porous(lbm, stream, precision, propagation, pack):
 
 
 def porous_variant(lbm, stream, precision, propagation, steps, pack, peak):
+    """The porous medium on a fluid list, autotuned (block size and link
+    encoding), then timed with the link table and with the run-indexed code
+    (reduced indirect addressing) at the chosen block size."""
     h = make_porous(lbm, stream, precision, propagation, pack)
+    timed = {}
     try:
         nf = lbm.lbm_fluid_count(h, 0)
+        table_bytes, ria_bytes = lbm.lbm_adjacency_bytes(h, 0)
         lbm.lbm_autotune(h, 4)
-        lbm.lbm_step(h, 4)
-        sec = time_steps(lbm, h, steps, stream)
+        chosen = lbm.lbm_get_run_indexing(h)
+        for ria in (chosen, not chosen):
+            lbm.lbm_set_run_indexing(h, ria)
+            lbm.lbm_step(h, 4)
+            timed[ria] = time_steps(lbm, h, steps, stream)
+        lbm.lbm_set_run_indexing(h, chosen)
+        tuning = lbm.lbm_get_tuning(h)
     finally:
         lbm.lbm_destroy(h)
-    mflups = nf * steps / sec / 1e6
-    elem = {lbm.LBM_F64: 8, lbm.LBM_F32_SHIFTED: 4, lbm.LBM_F16_SHIFTED: 2}[precision]
-    bpf = bytes_per_flup(elem, True, "pull" if propagation == lbm.LBM_PULL_TWO_GRID else "aa")
-    gbs = mflups * 1e6 * bpf / 1e9
-    return {"mflups": round(mflups, 1), "bytes_per_flup": bpf, "achieved_gbs": round(gbs, 1),
-            "roofline_frac": round(gbs / peak, 4), "steps": steps, "fluid_cells": nf,
+    elem = {lbm.LBM_F64: 8, lbm.LBM_F32_SHIFTED: 4, lbm.LBM_F16_SHIFTED: 2,
+            lbm.LBM_F16_SHIFTED_STOCHASTIC: 2}[precision]
+    prop = "pull" if propagation == lbm.LBM_PULL_TWO_GRID else "aa"
+    # index bytes per fluid update: pull reads the links every step, AA on odd steps only
+    index_share = 1.0 if prop == "pull" else 0.5
+    pdf_bpf = bytes_per_flup(elem, False, prop)
+    bpf = {True: pdf_bpf + index_share * ria_bytes / nf, False: pdf_bpf + index_share * table_bytes / nf}
+    out = {}
+    for ria, sec in timed.items():
+        mflups = nf * steps / sec / 1e6
+        gbs = mflups * 1e6 * bpf[ria] / 1e9
+        out["run_indexed" if ria else "link_table"] = {
+            "mflups": round(mflups, 1), "bytes_per_flup": round(bpf[ria], 1), "achieved_gbs": round(gbs, 1),
+            "roofline_frac": round(gbs / peak, 4)}
+    best = out["run_indexed" if chosen else "link_table"]
+    return {"mflups": best["mflups"], "bytes_per_flup": best["bytes_per_flup"], "achieved_gbs": best["achieved_gbs"],
+            "roofline_frac": best["roofline_frac"], "autotuned": {"threads": tuning[0], "run_indexing": chosen},
+            "by_encoding": out, "steps": steps, "fluid_cells": nf,
             "porosity": round(nf / float(np.prod(inputs.POROUS_256["dims"])), 4),
             "workload": "porous 256^3, spheres r 4-12, fluid list + int32 adjacency, half-way bounce-back"}
 
@@ -425,6 +447,8 @@ def run_sweep_only(args):
         nf = sum(lbm.lbm_fluid_count(h, k) for k in range(len(specs)))
     if args.tuning:
         lbm.lbm_set_tuning(h, *[int(v) for v in args.tuning.split(",")])
+    if args.run_indexing:
+        lbm.lbm_set_run_indexing(h, args.run_indexing == "on")
     lbm.lbm_step(h, args.warmup)
     sec = time_steps(lbm, h, args.steps, stream)
     lbm.lbm_destroy(h)
@@ -508,6 +532,10 @@ def run_gpu(args):
         variants["f64_list_pull_porous256"] = porous_variant(lbm, stream, lbm.LBM_F64, lbm.LBM_PULL_TWO_GRID, vs,
                                                              pack, peak)
         variants["f32_list_aa_porous256"] = porous_variant(lbm, stream, lbm.LBM_F32_SHIFTED, lbm.LBM_AA_INPLACE, vs,
+                                                           pack, peak)
+        variants["f32_list_pull_porous256"] = porous_variant(lbm, stream, lbm.LBM_F32_SHIFTED, lbm.LBM_PULL_TWO_GRID,
+                                                             vs, pack, peak)
+        variants["f16_list_aa_porous256"] = porous_variant(lbm, stream, lbm.LBM_F16_SHIFTED, lbm.LBM_AA_INPLACE, vs,
                                                            pack, peak)
         variants["f32_batched_512"] = batch_variant(lbm, stream, min(args.steps, 100), peak)
         variants["f32_aa_geometries256"] = geometry_sweep(lbm, stream, min(args.steps, 50))
@@ -622,6 +650,8 @@ def main():
                     help="profiling (with --sweep-only)")
     ap.add_argument("--batch-count", type=int, default=512, help="profiling: lattices in the batch workload")
     ap.add_argument("--tuning", default="", help="profiling: threads,cells_per_thread,ctas_per_sm")
+    ap.add_argument("--run-indexing", default="", choices=["", "on", "off"],
+                    help="profiling: fluid lists read the run-indexed links (on) or the link table (off)")
     args = ap.parse_args()
     if args.dims:
         global DIMS

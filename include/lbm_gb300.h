@@ -183,6 +183,26 @@ int lbm_init_equilibrium(lbm_handle h, int32_t lattice, const double* rho, const
  * runs of steps are replayed from captured CUDA graphs. */
 int lbm_step(lbm_handle h, int32_t n);
 
+/* Reduced indirect addressing (RIA, Sec. 3 "AA Pattern Kernels": a run-length
+ * code of the adjacency so that consecutive nodes sharing an access pattern
+ * need no lookup of their own). For indirectly addressed lattices the library
+ * keeps, next to the link table, a code per chunk of 32 consecutive list nodes
+ * and direction: a mask of the nodes that start a run of consecutive links,
+ * and the first link of each run. With enable = 1 (the default) the
+ * single-lattice list sweeps (pull, and the odd AA step) read the code instead
+ * of the table; results are identical either way. The batched sweep always
+ * reads the table. lbm_autotune tries both. The code is built and checked
+ * against the table when the geometry is set; it costs 144 bytes per 32 nodes
+ * plus 4 bytes per run. LBM_ERR_ARG unless enable is 0 or 1. */
+int lbm_set_run_indexing(lbm_handle h, int32_t enable);
+int lbm_get_run_indexing(lbm_handle h, int32_t* enabled);
+
+/* Index bytes one sweep over lattice `lattice` reads per full pass over its
+ * nodes: out[0] for the link table (18 x 4 bytes per fluid node), out[1] for
+ * the run-indexed code (headers and run pool). Both 0 for direct addressing.
+ * LBM_ERR_STATE before the geometry is set. */
+int lbm_adjacency_bytes(lbm_handle h, int32_t lattice, int64_t out[2]);
+
 /* Seed and sweep number of the random bits of LBM_F16_SHIFTED_STOCHASTIC
  * storage (see lbm_precision). Lattice l of a batch uses seed + l. `sweep` is
  * the number t that the next time step draws with (t >= 0); every step then

@@ -38,6 +38,11 @@ struct Lattice {
   int32_t* cell_of = nullptr;
   int32_t* list_index = nullptr;
   int* status = nullptr;   // the handle's device status word
+  // run-indexed code of `link` (lbm_ria.cu), indirect lattices only
+  uint2* ria_head = nullptr;
+  uint32_t* ria_pool = nullptr;
+  uint32_t* ria_chunk_start = nullptr;
+  int64_t ria_pool_entries = 0;
   bool has_halfway = false, has_fullway = false;
   bool geometry = false, params = false, init = false;
   double omega = 1.0, Lambda = 0.25;
@@ -75,6 +80,7 @@ struct lbm_lattice_s {
   int phase = 0;         // total steps mod 2: AA parity, pull buffer holding the state
   bool poisoned = false;
   int threads = 256, cells_per_thread = 1, ctas_per_sm = 0;
+  bool run_indexing = true;   // staged list sweeps read the run-indexed links
   // batch work list: one descriptor per lattice and the tiles (rebuilt lazily)
   void* d_lat = nullptr;
   size_t d_lat_bytes = 0;
@@ -271,10 +277,50 @@ void free_storage(lbm_handle h, Lattice& L) {
     p = nullptr;
   }
   h->dfree(L.link, (size_t)18 * L.stride * sizeof(uint32_t));
+  const int64_t chunks = ria_chunks(L.nf);
+  h->dfree(L.ria_head, (size_t)chunks * 18 * sizeof(uint2));
+  h->dfree(L.ria_pool, (size_t)(L.ria_pool_entries + 4) * sizeof(uint32_t));
+  h->dfree(L.ria_chunk_start, (size_t)(chunks + 1) * sizeof(uint32_t));
+  L.ria_head = nullptr;
+  L.ria_pool = nullptr;
+  L.ria_chunk_start = nullptr;
+  L.ria_pool_entries = 0;
   h->dfree(L.cell_of, (size_t)L.nf * sizeof(int32_t));
   h->dfree(L.list_index, (size_t)L.N * sizeof(int32_t));
   L.link = nullptr;
   L.cell_of = L.list_index = nullptr;
+}
+
+// The run-indexed code of an indirect lattice's links (lbm_ria.cu): count the
+// runs, size the pool, fill it, and check that it reproduces every link.
+int build_run_index(lbm_handle h, Lattice& L) {
+  const int64_t chunks = ria_chunks(L.nf);
+  if (chunks == 0) return LBM_OK;
+  L.ria_chunk_start = static_cast<uint32_t*>(h->dalloc((size_t)(chunks + 1) * sizeof(uint32_t)));
+  L.ria_head = static_cast<uint2*>(h->dalloc((size_t)chunks * 18 * sizeof(uint2)));
+  if (!L.ria_chunk_start || !L.ria_head) return fail(LBM_ERR_OOM, "allocation of the run-indexed adjacency failed");
+  Scratch sc(h, 2 * sizeof(int64_t));
+  if (!sc.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
+  const LatticeView v = L.view();
+  LBM_CUDA(h, launch_ria_count(v, L.ria_chunk_start, sc.as<int64_t>(), h->stream), "run count");
+  int64_t total = 0;
+  LBM_CUDA(h, cudaMemcpyAsync(&total, sc.p, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream), "copy run count");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "run count sync");
+  if (total <= 0 || total > 18 * L.nf) return fail(LBM_ERR_STATE, "run count of the adjacency out of range");
+  L.ria_pool_entries = total;
+  // 4 spare entries: a tile's pool slice is copied rounded out to 16 bytes
+  L.ria_pool = static_cast<uint32_t*>(h->dalloc((size_t)(total + 4) * sizeof(uint32_t)));
+  if (!L.ria_pool) return fail(LBM_ERR_OOM, "allocation of the run-indexed adjacency failed");
+  LBM_CUDA(h, cudaMemsetAsync(L.ria_pool, 0, (size_t)(total + 4) * sizeof(uint32_t), h->stream), "memset pool");
+  LBM_CUDA(h, launch_ria_fill(v, L.ria_chunk_start, L.ria_head, L.ria_pool, h->stream), "run fill");
+  unsigned long long* d_bad = reinterpret_cast<unsigned long long*>(sc.as<int64_t>() + 1);
+  LBM_CUDA(h, cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), h->stream), "memset");
+  LBM_CUDA(h, launch_ria_verify(v, L.ria_head, L.ria_pool, (uint32_t)total, d_bad, h->stream), "run verify");
+  unsigned long long bad = 1;
+  LBM_CUDA(h, cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream), "copy verify");
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream), "run verify sync");
+  if (bad != 0) return fail(LBM_ERR_STATE, "run-indexed adjacency does not reproduce the link table");
+  return LBM_OK;
 }
 
 // Validate the flags now on the device, build lists and allocate storage.
@@ -330,6 +376,7 @@ int finish_geometry(lbm_handle h, Lattice& L) {
     LBM_CUDA(h, cudaMemcpyAsync(&nf_check, nfbuf.p, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream), "copy nf");
     LBM_CUDA(h, cudaStreamSynchronize(h->stream), "adjacency sync");
     if (nf_check != L.nf) return fail(LBM_ERR_STATE, "fluid compaction disagrees with the flag count");
+    if (int rc = build_run_index(h, L)) return rc;
   }
   L.geometry = true;
   return LBM_OK;
@@ -364,6 +411,11 @@ int sm_count() {
 // The kernel view of lattice k with the stochastic format's stream attached.
 LatticeView sweep_view(lbm_handle h, size_t k) {
   LatticeView v = h->lat[k].view();
+  if (h->run_indexing && v.indirect) {
+    v.ria_head = h->lat[k].ria_head;
+    v.ria_pool = h->lat[k].ria_pool;
+    v.ria_chunk_start = h->lat[k].ria_chunk_start;
+  }
   v.sr_seed = h->sr_seed + (unsigned long long)k;
   v.sweep_ctr = h->d_sweep;
   return v;
@@ -601,6 +653,35 @@ int lbm_step(lbm_handle h, int32_t n) {
   return step_impl(h, n, true);
 }
 
+int lbm_set_run_indexing(lbm_handle h, int32_t enable) {
+  if (int rc = check_handle(h)) return rc;
+  if (enable != 0 && enable != 1) return fail(LBM_ERR_ARG, "enable must be 0 or 1");
+  h->drop_graphs();
+  h->run_indexing = enable != 0;
+  return LBM_OK;
+}
+
+int lbm_adjacency_bytes(lbm_handle h, int32_t lattice, int64_t out[2]) {
+  if (int rc = check_lattice(h, lattice)) return rc;
+  if (!out) return fail(LBM_ERR_ARG, "null output");
+  const Lattice& L = h->lat[lattice];
+  if (!L.geometry) return fail(LBM_ERR_STATE, "no geometry set");
+  if (!L.indirect()) {
+    out[0] = out[1] = 0;
+    return LBM_OK;
+  }
+  out[0] = 18 * L.nf * (int64_t)sizeof(uint32_t);
+  out[1] = ria_chunks(L.nf) * 18 * (int64_t)sizeof(uint2) + L.ria_pool_entries * (int64_t)sizeof(uint32_t);
+  return LBM_OK;
+}
+
+int lbm_get_run_indexing(lbm_handle h, int32_t* enabled) {
+  if (int rc = check_handle(h)) return rc;
+  if (!enabled) return fail(LBM_ERR_ARG, "null output");
+  *enabled = h->run_indexing ? 1 : 0;
+  return LBM_OK;
+}
+
 int lbm_set_stochastic_rounding(lbm_handle h, uint64_t seed, int64_t sweep) {
   if (int rc = check_handle(h)) return rc;
   if (h->prec != LBM_F16_SHIFTED_STOCHASTIC)
@@ -802,19 +883,21 @@ int lbm_autotune(lbm_handle h, int32_t steps) {
   }
   struct Shape {
     int threads, cpt, ctas;
+    bool ria;
   };
   std::vector<Shape> shapes;
   if (h->batched()) {
     for (int t : {128, 256, 512})
       for (int c : {1, 2, 4, 8})
-        for (int g : {0, 2, 4, 8}) shapes.push_back({t, c, g});
+        for (int g : {0, 2, 4, 8}) shapes.push_back({t, c, g, h->run_indexing});
   } else {
     const bool dense = !h->lat[0].indirect();
     for (int t : {64, 128, 192, 256, 384, 512})
       for (int c : {1, 2})
-        if (c == 1 || dense) shapes.push_back({t, c, 0});
+        for (int r : {1, 0})
+          if ((c == 1 || dense) && (r == 1 || !dense)) shapes.push_back({t, c, 0, dense ? h->run_indexing : r == 1});
   }
-  Shape best{h->threads, h->cells_per_thread, h->ctas_per_sm};
+  Shape best{h->threads, h->cells_per_thread, h->ctas_per_sm, h->run_indexing};
   float best_ms = 1e30f;
   int rc = LBM_OK;
   for (const Shape& sh : shapes) {
@@ -822,6 +905,7 @@ int lbm_autotune(lbm_handle h, int32_t steps) {
     h->threads = sh.threads;
     h->cells_per_thread = sh.cpt;
     h->ctas_per_sm = sh.ctas;
+    h->run_indexing = sh.ria;
     rc = step_impl(h, 2, false);   // warm-up (and table rebuild)
     if (rc == LBM_OK) {
       cudaEventRecord(h->ev0, h->stream);
@@ -841,6 +925,7 @@ int lbm_autotune(lbm_handle h, int32_t steps) {
   h->threads = best.threads;
   h->cells_per_thread = best.cpt;
   h->ctas_per_sm = best.ctas;
+  h->run_indexing = best.ria;
   h->drop_graphs();
   h->phase = phase0;
   h->steps = steps0;

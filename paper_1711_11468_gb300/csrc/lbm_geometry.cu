@@ -207,6 +207,11 @@ cudaError_t launch_compact(const uint8_t* d_flags, int64_t n, int32_t* d_list_in
   return cudaGetLastError();
 }
 
+cudaError_t launch_exclusive_scan(int32_t* data, int64_t n, int64_t* d_total, cudaStream_t s) {
+  k_scan_tiles<<<1, kScanThreads, 0, s>>>(data, n, d_total);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_links(const LatticeView& v, const int32_t* d_list_index, bool aa, uint32_t* d_link,
                          cudaStream_t s) {
   if (v.n_nodes == 0) return cudaSuccess;

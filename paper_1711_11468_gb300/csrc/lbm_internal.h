@@ -47,6 +47,11 @@ struct LatticeView {
   const int32_t* cell_of = nullptr;   // [Nf], indirect only
   const int32_t* list_index = nullptr;  // [N] node of each cell or -1, indirect only
   int* status = nullptr;                // device status word of the handle (timeouts)
+  // Indirect only, optional: the run-indexed code of `link` (lbm_ria.cu); the
+  // staged list sweeps read it instead of the table when ria_head is set.
+  const uint2* ria_head = nullptr;            // [chunks][18] {run-start mask, pool start}
+  const uint32_t* ria_pool = nullptr;         // first link of each run
+  const uint32_t* ria_chunk_start = nullptr;  // [chunks + 1] pool start of each chunk
   // FP16 stochastic format only: the lattice's seed and the handle's pair of
   // sweep counters (a sweep of parity q reads word q and writes word q ^ 1).
   unsigned long long sr_seed = 0;
@@ -107,7 +112,21 @@ int moments_blocks(const LatticeView& v);
 cudaError_t launch_moments(const LatticeView& v, Layout layout, const void* src, double* partials, int blocks,
                            double* out, cudaStream_t s);
 
+// ------------------------------------------------ run-indexed adjacency (RIA)
+// Chunks of 32 list nodes. Count: chunk_start[chunks + 1] receives the
+// exclusive prefix of the runs per chunk and, last, the pool size (also in
+// *d_total). Fill: head[chunks][18] and pool[pool size]. Verify: adds the number
+// of links the code does not reproduce to *d_mismatches.
+int64_t ria_chunks(int64_t nf);
+cudaError_t launch_ria_count(const LatticeView& v, uint32_t* chunk_start, int64_t* d_total, cudaStream_t s);
+cudaError_t launch_ria_fill(const LatticeView& v, const uint32_t* chunk_start, uint2* head, uint32_t* pool,
+                            cudaStream_t s);
+cudaError_t launch_ria_verify(const LatticeView& v, const uint2* head, const uint32_t* pool, uint32_t pool_entries,
+                              unsigned long long* d_mismatches, cudaStream_t s);
+
 // ------------------------------------------------------------- geometry
+// Exclusive prefix sum of data[n] in place (single CTA, int64 carry); the total to *d_total.
+cudaError_t launch_exclusive_scan(int32_t* data, int64_t n, int64_t* d_total, cudaStream_t s);
 cudaError_t launch_voxelize_spheres(int nx, int ny, int nz, const int32_t* d_spheres, int nspheres,
                                     uint8_t value, uint8_t* d_flags, cudaStream_t s);
 // Fluid compaction: list_index[N] (-1 for solid), cell_of[Nf]; block sums in

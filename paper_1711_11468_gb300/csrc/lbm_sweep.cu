@@ -423,6 +423,134 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_list_staged(const S* __re
       if (pending[b] && !mbar_wait_bounded(&bar[b], parity[b])) atomicOr(status, kStatusWaitTimeout);
 }
 
+// The same persistent, double-buffered sweep reading the run-indexed code of
+// the links (lbm_ria.cu) instead of the table: per tile of T nodes (T/32
+// chunks) one bulk copy brings the chunks' headers (144 bytes each) and one the
+// chunks' slice of the run pool, rounded out to 16-byte boundaries. Each lane
+// decodes its 18 links from shared memory. Results are those of the table
+// kernel, bit for bit: only the way the offsets are found differs.
+constexpr size_t staged_ria_smem_bytes(int threads) {
+  return (size_t)2 * ((size_t)(threads / 32) * (Q - 1) * sizeof(uint2) + ((size_t)(Q - 1) * threads + 8) * sizeof(uint32_t));
+}
+
+template <typename S, int KIND>
+__global__ void __launch_bounds__(kStagedMaxThreads) k_list_staged_ria(const S* __restrict__ src, S* __restrict__ dst,
+                                                                       const uint2* __restrict__ head,
+                                                                       const uint32_t* __restrict__ pool,
+                                                                       const uint32_t* __restrict__ chunk_start,
+                                                                       int64_t nf, int64_t stride, ParamsT<S> lp,
+                                                                       int* status) {
+  const ParamsT<S> p = begin_sweep<S>(lp);
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bar[2];
+  __shared__ uint32_t pool_base[2];
+  __shared__ int abort_flag;
+  const int T = blockDim.x, C = T / 32;
+  const int j = threadIdx.x, lane = j & 31, w = j >> 5;
+  uint2* shead[2] = {reinterpret_cast<uint2*>(smem), reinterpret_cast<uint2*>(smem) + (Q - 1) * C};
+  uint32_t* spool0 = reinterpret_cast<uint32_t*>(shead[1] + (Q - 1) * C);
+  uint32_t* spool[2] = {spool0, spool0 + (Q - 1) * T + 8};
+  const int64_t chunks = (nf + 31) / 32;
+  const int64_t ntiles = (nf + T - 1) / T;
+  if (j == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    abort_flag = 0;
+  }
+  __syncthreads();
+  auto issue = [&](int64_t tile, int b) {
+    const int64_t c0 = tile * C;
+    const int64_t c1 = c0 + C < chunks ? c0 + C : chunks;
+    const uint32_t hbytes = (uint32_t)((c1 - c0) * (Q - 1) * sizeof(uint2));   // 144 per chunk
+    const uint32_t a0 = chunk_start[c0] & ~3u, a1 = (chunk_start[c1] + 3u) & ~3u;
+    const uint32_t pbytes = (a1 - a0) * (uint32_t)sizeof(uint32_t);
+    pool_base[b] = a0;
+    mbar_arrive_expect_tx(&bar[b], hbytes + pbytes);
+    bulk_copy_g2s(shead[b], head + c0 * (Q - 1), hbytes, &bar[b]);
+    bulk_copy_g2s(spool[b], pool + a0, pbytes, &bar[b]);
+  };
+  const unsigned le = (2u << lane) - 1u;   // lanes 0..lane
+  uint32_t parity[2] = {0u, 0u};
+  bool pending[2] = {false, false};
+  int it = 0;
+  int64_t t = blockIdx.x;
+  if (j == 0 && t < ntiles) {
+    issue(t, 0);
+    pending[0] = true;
+  }
+  for (; t < ntiles; t += gridDim.x, ++it) {
+    const int b = it & 1;
+    const int64_t tn = t + gridDim.x;
+    if (j == 0 && tn < ntiles) {
+      fence_proxy_async_smem();
+      issue(tn, b ^ 1);
+      pending[b ^ 1] = true;
+    }
+    const bool ok = mbar_wait_bounded(&bar[b], parity[b]);
+    if (ok) {
+      parity[b] ^= 1u;
+      if (j == 0) pending[b] = false;
+    }
+    if (!ok) {
+      atomicOr(status, kStatusWaitTimeout);
+      abort_flag = 1;
+    } else {
+      const int64_t k = t * T + j;
+      if (k < nf) {
+        const uint2* hd = shead[b] + w * (Q - 1);
+        const uint32_t* pl = spool[b];
+        const uint32_t pb = pool_base[b];
+        uint32_t off[Q];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          const uint2 h = hd[i - 1];
+          const unsigned below = h.x & le;
+          off[i] = pl[h.y - pb + (uint32_t)__popc(below) - 1u] + (uint32_t)(lane - 31 + __clz(below));
+        }
+        RawT<S> f[Q];
+        if (KIND == kPull) {
+          f[0] = Storage<S>::load(src + k);
+#pragma unroll
+          for (int i = 1; i < Q; ++i) f[i] = Storage<S>::load(src + off[i]);
+          Storage<S>::relax(f, p, (uint32_t)k);
+#pragma unroll
+          for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + k, f[i]);
+        } else {
+          f[0] = Storage<S>::load(dst + k);
+#pragma unroll
+          for (int i = 1; i < Q; ++i) f[i] = Storage<S>::load(dst + off[i]);
+          Storage<S>::relax(f, p, (uint32_t)k);
+          Storage<S>::store(dst + k, f[0]);
+#pragma unroll
+          for (int i = 1; i < Q; ++i) Storage<S>::store(dst + off[opp(i)], f[i]);
+        }
+      }
+    }
+    __syncthreads();
+    if (abort_flag) break;
+  }
+  if (j == 0)
+    for (int b = 0; b < 2; ++b)
+      if (pending[b] && !mbar_wait_bounded(&bar[b], parity[b])) atomicOr(status, kStatusWaitTimeout);
+}
+
+template <typename S, int KIND>
+int staged_ria_grid(int threads, int64_t ntiles) {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_list_staged_ria<S, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)staged_ria_smem_bytes(kStagedMaxThreads));
+  });
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_list_staged_ria<S, KIND>, threads,
+                                                staged_ria_smem_bytes(threads));
+  const int64_t g = (int64_t)std::max(1, sms) * std::max(1, per_sm);
+  return (int)std::min<int64_t>(g, ntiles);
+}
+
 template <typename S, int KIND>
 int staged_grid(int threads, int64_t ntiles) {
   static std::once_flag once;
@@ -510,9 +638,14 @@ cudaError_t sweep_typed(const LatticeView& v, SweepKind kind, int parity, const 
     if (v.n_nodes == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((v.n_nodes + threads - 1) / threads);
     const int64_t ntiles = blocks;
+    const bool ria = v.status && v.ria_head && v.ria_pool && v.ria_chunk_start;
     switch (kind) {
       case kPull:
-        if (v.status)
+        if (ria)
+          k_list_staged_ria<S, kPull><<<staged_ria_grid<S, kPull>(threads, ntiles), threads,
+                                         staged_ria_smem_bytes(threads), s>>>(
+              src, dst, v.ria_head, v.ria_pool, v.ria_chunk_start, v.n_nodes, v.stride, p, v.status);
+        else if (v.status)
           k_list_staged<S, kPull><<<staged_grid<S, kPull>(threads, ntiles), threads, staged_smem_bytes(threads), s>>>(
               src, dst, v.link, v.n_nodes, v.stride, p, v.status);
         else
@@ -522,7 +655,11 @@ cudaError_t sweep_typed(const LatticeView& v, SweepKind kind, int parity, const 
         k_list_aa_even<S><<<blocks, threads, 0, s>>>(dst, v.n_nodes, v.stride, p);
         break;
       case kAAOdd:
-        if (v.status)
+        if (ria)
+          k_list_staged_ria<S, kAAOdd><<<staged_ria_grid<S, kAAOdd>(threads, ntiles), threads,
+                                          staged_ria_smem_bytes(threads), s>>>(
+              dst, dst, v.ria_head, v.ria_pool, v.ria_chunk_start, v.n_nodes, v.stride, p, v.status);
+        else if (v.status)
           k_list_staged<S, kAAOdd><<<staged_grid<S, kAAOdd>(threads, ntiles), threads, staged_smem_bytes(threads),
                                       s>>>(dst, dst, v.link, v.n_nodes, v.stride, p, v.status);
         else

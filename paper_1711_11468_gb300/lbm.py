@@ -81,6 +81,9 @@ def load(path: str | None = None):
         "lbm_step": [H, i32],
         "lbm_synchronize": [H],
         "lbm_set_stochastic_rounding": [H, ctypes.c_uint64, i64],
+        "lbm_set_run_indexing": [H, i32],
+        "lbm_get_run_indexing": [H, ctypes.POINTER(i32)],
+        "lbm_adjacency_bytes": [H, i32, ctypes.POINTER(i64)],
         "lbm_steps_done": [H, ctypes.POINTER(i64)],
         "lbm_read_pdfs": [H, i32, vp, sz],
         "lbm_write_pdfs": [H, i32, vp, sz],
@@ -229,6 +232,23 @@ def lbm_init_equilibrium(h: Handle, lattice: int, rho=None, u=None):
 
 def lbm_step(h: Handle, n: int):
     _check(load().lbm_step(h, int(n)))
+
+
+def lbm_set_run_indexing(h: Handle, enable: bool):
+    _check(load().lbm_set_run_indexing(h, 1 if enable else 0))
+
+
+def lbm_adjacency_bytes(h: Handle, lattice: int = 0):
+    """(link-table bytes, run-indexed code bytes) of an indirectly addressed lattice."""
+    out = (ctypes.c_int64 * 2)()
+    _check(load().lbm_adjacency_bytes(h, lattice, out))
+    return int(out[0]), int(out[1])
+
+
+def lbm_get_run_indexing(h: Handle) -> bool:
+    v = ctypes.c_int32()
+    _check(load().lbm_get_run_indexing(h, ctypes.byref(v)))
+    return bool(v.value)
 
 
 def lbm_set_stochastic_rounding(h: Handle, seed: int, sweep: int = 0):
