@@ -393,21 +393,26 @@ def microbench(lbm, stream, elem: int = 8, n: int = 1 << 24, reps: int = 5):
     return out
 
 
-def variant(lbm, stream, precision, propagation, steps, nf, peak):
+def variant(lbm, stream, precision, propagation, steps, nf, peak, steps_per_pass=0):
+    """The duct at another storage format or propagation, autotuned; with
+    steps_per_pass set, temporal blocking is fixed to it after tuning."""
     h, _ = make_duct(lbm, stream, precision, propagation)
     try:
         lbm.lbm_autotune(h, 4)
+        if steps_per_pass:
+            lbm.lbm_set_temporal_blocking(h, steps_per_pass)
         lbm.lbm_step(h, 4)
         sec = time_steps(lbm, h, steps, stream)
+        spp = lbm.lbm_get_temporal_blocking(h)
     finally:
         lbm.lbm_destroy(h)
     mflups = nf * steps / sec / 1e6
     elem = {lbm.LBM_F64: 8, lbm.LBM_F32_SHIFTED: 4, lbm.LBM_F16_SHIFTED: 2, lbm.LBM_F64_DOUBLE_FLOAT: 8,
             lbm.LBM_F32_SHIFTED_DOUBLE_FLOAT: 4, lbm.LBM_F16_SHIFTED_STOCHASTIC: 2}[precision]
-    bpf = bytes_per_flup(elem, False, "pull" if propagation == lbm.LBM_PULL_TWO_GRID else "aa")
+    bpf = bytes_per_flup(elem, False, "pull" if propagation == lbm.LBM_PULL_TWO_GRID else "aa") / spp
     gbs = mflups * 1e6 * bpf / 1e9
     return {"mflups": round(mflups, 1), "bytes_per_flup": bpf, "achieved_gbs": round(gbs, 1),
-            "roofline_frac": round(gbs / peak, 4), "steps": steps}
+            "roofline_frac": round(gbs / peak, 4), "steps": steps, "steps_per_pass": spp}
 
 
 def run_sweep_only(args):
@@ -449,6 +454,8 @@ def run_sweep_only(args):
         lbm.lbm_set_tuning(h, *[int(v) for v in args.tuning.split(",")])
     if args.run_indexing:
         lbm.lbm_set_run_indexing(h, args.run_indexing == "on")
+    if args.steps_per_pass:
+        lbm.lbm_set_temporal_blocking(h, args.steps_per_pass)
     lbm.lbm_step(h, args.warmup)
     sec = time_steps(lbm, h, args.steps, stream)
     lbm.lbm_destroy(h)
@@ -523,6 +530,10 @@ def run_gpu(args):
         variants["f16_shifted_aa"] = variant(lbm, stream, lbm.LBM_F16_SHIFTED, lbm.LBM_AA_INPLACE, vs, nf, peak)
         variants["f16_shifted_stochastic_aa"] = variant(lbm, stream, lbm.LBM_F16_SHIFTED_STOCHASTIC,
                                                         lbm.LBM_AA_INPLACE, vs, nf, peak)
+        variants["f32_shifted_pull_two_steps_per_pass"] = variant(lbm, stream, lbm.LBM_F32_SHIFTED,
+                                                                  lbm.LBM_PULL_TWO_GRID, vs, nf, peak, 2)
+        variants["f16_shifted_pull_two_steps_per_pass"] = variant(lbm, stream, lbm.LBM_F16_SHIFTED,
+                                                                  lbm.LBM_PULL_TWO_GRID, vs, nf, peak, 2)
         variants["f32_shifted_double_float_aa"] = variant(lbm, stream, lbm.LBM_F32_SHIFTED_DOUBLE_FLOAT,
                                                           lbm.LBM_AA_INPLACE, vs, nf, peak)
         c2 = inputs.POROUS_256
@@ -650,6 +661,8 @@ def main():
                     help="profiling (with --sweep-only)")
     ap.add_argument("--batch-count", type=int, default=512, help="profiling: lattices in the batch workload")
     ap.add_argument("--tuning", default="", help="profiling: threads,cells_per_thread,ctas_per_sm")
+    ap.add_argument("--steps-per-pass", type=int, default=0, choices=[0, 1, 2],
+                    help="profiling: temporal blocking of full-array pull sweeps (2 = two steps per launch)")
     ap.add_argument("--run-indexing", default="", choices=["", "on", "off"],
                     help="profiling: fluid lists read the run-indexed links (on) or the link table (off)")
     args = ap.parse_args()

@@ -81,6 +81,10 @@ struct lbm_lattice_s {
   bool poisoned = false;
   int threads = 256, cells_per_thread = 1, ctas_per_sm = 0;
   bool run_indexing = true;   // staged list sweeps read the run-indexed links
+  int steps_per_pass = 1;     // 2: temporal blocking (single full-array pull lattice)
+  bool two_step() const {
+    return steps_per_pass == 2 && lat.size() == 1 && prop == LBM_PULL_TWO_GRID && !lat[0].indirect();
+  }
   // batch work list: one descriptor per lattice and the tiles (rebuilt lazily)
   void* d_lat = nullptr;
   size_t d_lat_bytes = 0;
@@ -482,12 +486,25 @@ cudaError_t issue_step(lbm_handle h, int phase, cudaStream_t s) {
   return cudaSuccess;
 }
 
+// Two time steps of a temporally blocked lattice in one launch, from buffer
+// `phase` into the other one (the state then sits in buffer phase ^ 1).
+cudaError_t issue_two_steps(lbm_handle h, int phase, cudaStream_t s) {
+  Lattice& L = h->lat[0];
+  return launch_sweep_pull2(sweep_view(h, 0), phase, L.pdf[phase], L.pdf[phase ^ 1], L.trt, h->threads, s);
+}
+
 cudaError_t capture_graph(lbm_handle h, int phase, cudaGraphExec_t* exec) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
   cudaError_t le = cudaSuccess;
-  for (int t = 0; t < kGraphSteps && le == cudaSuccess; ++t) le = issue_step(h, (phase + t) & 1, h->capture_stream);
+  if (h->two_step()) {
+    // kGraphSteps / 2 launches, an even number: the state returns to buffer `phase`
+    for (int t = 0; t < kGraphSteps / 2 && le == cudaSuccess; ++t)
+      le = issue_two_steps(h, (phase + t) & 1, h->capture_stream);
+  } else {
+    for (int t = 0; t < kGraphSteps && le == cudaSuccess; ++t) le = issue_step(h, (phase + t) & 1, h->capture_stream);
+  }
   e = cudaStreamEndCapture(h->capture_stream, &g);
   if (le != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -509,6 +526,13 @@ int step_impl(lbm_handle h, int32_t n, bool use_graphs) {
       if (!g) LBM_CUDA(h, capture_graph(h, h->phase, &g), "graph capture");
       LBM_CUDA(h, cudaGraphLaunch(g, h->stream), "graph launch");
       done += kGraphSteps;   // even: phase unchanged
+    }
+  }
+  // phase: the AA parity, or for pull the buffer that holds the state (one flip per launch)
+  if (h->two_step()) {
+    for (; n - done >= 2; done += 2) {
+      LBM_CUDA(h, issue_two_steps(h, h->phase, h->stream), "two-step sweep launch");
+      h->phase ^= 1;
     }
   }
   for (; done < n; ++done) {
@@ -651,6 +675,24 @@ int lbm_step(lbm_handle h, int32_t n) {
   if (n < 0) return fail(LBM_ERR_ARG, "n must be >= 0");
   if (int rc = ready_to_step(h)) return rc;
   return step_impl(h, n, true);
+}
+
+int lbm_set_temporal_blocking(lbm_handle h, int32_t steps_per_pass) {
+  if (int rc = check_handle(h)) return rc;
+  if (steps_per_pass != 1 && steps_per_pass != 2) return fail(LBM_ERR_ARG, "steps_per_pass must be 1 or 2");
+  if (steps_per_pass == 2 &&
+      (h->batched() || h->prop != LBM_PULL_TWO_GRID || h->lat[0].desc.addressing != LBM_DIRECT))
+    return fail(LBM_ERR_UNSUPPORTED, "temporal blocking serves a single full-array lattice with two-grid pull");
+  h->drop_graphs();
+  h->steps_per_pass = steps_per_pass;
+  return LBM_OK;
+}
+
+int lbm_get_temporal_blocking(lbm_handle h, int32_t* steps_per_pass) {
+  if (int rc = check_handle(h)) return rc;
+  if (!steps_per_pass) return fail(LBM_ERR_ARG, "null output");
+  *steps_per_pass = h->steps_per_pass;
+  return LBM_OK;
 }
 
 int lbm_set_run_indexing(lbm_handle h, int32_t enable) {
@@ -884,20 +926,24 @@ int lbm_autotune(lbm_handle h, int32_t steps) {
   struct Shape {
     int threads, cpt, ctas;
     bool ria;
+    int spp;   // steps per pass
   };
   std::vector<Shape> shapes;
   if (h->batched()) {
     for (int t : {128, 256, 512})
       for (int c : {1, 2, 4, 8})
-        for (int g : {0, 2, 4, 8}) shapes.push_back({t, c, g, h->run_indexing});
+        for (int g : {0, 2, 4, 8}) shapes.push_back({t, c, g, h->run_indexing, 1});
   } else {
     const bool dense = !h->lat[0].indirect();
     for (int t : {64, 128, 192, 256, 384, 512})
       for (int c : {1, 2})
         for (int r : {1, 0})
-          if ((c == 1 || dense) && (r == 1 || !dense)) shapes.push_back({t, c, 0, dense ? h->run_indexing : r == 1});
+          if ((c == 1 || dense) && (r == 1 || !dense))
+            shapes.push_back({t, c, 0, dense ? h->run_indexing : r == 1, 1});
+    if (dense && h->prop == LBM_PULL_TWO_GRID)
+      for (int t : {128, 256, 512}) shapes.push_back({t, 1, 0, h->run_indexing, 2});
   }
-  Shape best{h->threads, h->cells_per_thread, h->ctas_per_sm, h->run_indexing};
+  Shape best{h->threads, h->cells_per_thread, h->ctas_per_sm, h->run_indexing, h->steps_per_pass};
   float best_ms = 1e30f;
   int rc = LBM_OK;
   for (const Shape& sh : shapes) {
@@ -906,6 +952,7 @@ int lbm_autotune(lbm_handle h, int32_t steps) {
     h->cells_per_thread = sh.cpt;
     h->ctas_per_sm = sh.ctas;
     h->run_indexing = sh.ria;
+    h->steps_per_pass = sh.spp;
     rc = step_impl(h, 2, false);   // warm-up (and table rebuild)
     if (rc == LBM_OK) {
       cudaEventRecord(h->ev0, h->stream);
@@ -926,6 +973,7 @@ int lbm_autotune(lbm_handle h, int32_t steps) {
   h->cells_per_thread = best.cpt;
   h->ctas_per_sm = best.ctas;
   h->run_indexing = best.ria;
+  h->steps_per_pass = best.spp;
   h->drop_graphs();
   h->phase = phase0;
   h->steps = steps0;

@@ -153,7 +153,9 @@ __device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
 //            Raw values are the FP16 bit patterns, so that moving them (and
 //            reversing them at full-way solids) needs no conversion.
 // relax(f, p, node) is the entry point of the sweeps; node numbers the node's
-// random stream and only h16sr uses it.
+// random stream and only h16sr uses it. unpack / pack convert between a stored
+// element and its raw register value exactly as load / store do, for copies
+// kept in shared memory.
 // The shift keeps the collided magnitudes near the small departures that carry
 // the flow instead of near w_i.
 struct f64df {
@@ -180,6 +182,8 @@ struct Storage<double> {
   __device__ __forceinline__ static void relax(Raw (&f)[Q], const Params& p, uint32_t = 0) {
     collide<A, false>(f, p);
   }
+  __device__ __forceinline__ static Raw unpack(double v) { return v; }
+  __device__ __forceinline__ static double pack(Raw v) { return v; }
   __device__ __forceinline__ static double to_f64(double v, int) { return v; }
   __device__ __forceinline__ static double from_f64(double f, int) { return f; }
 };
@@ -195,6 +199,8 @@ struct Storage<float> {
   __device__ __forceinline__ static void relax(Raw (&f)[Q], const Params& p, uint32_t = 0) {
     collide<A, true>(f, p);
   }
+  __device__ __forceinline__ static Raw unpack(float v) { return v; }
+  __device__ __forceinline__ static float pack(Raw v) { return v; }
   __device__ __forceinline__ static double to_f64(float v, int i) { return weight(i) + (double)v; }
   __device__ __forceinline__ static float from_f64(double f, int i) { return __double2float_rn(f - weight(i)); }
 };
@@ -214,6 +220,8 @@ struct Storage<__half> {
   __device__ __forceinline__ static void relax(Raw (&f)[Q], const Params& p, uint32_t = 0) {
     collide<A, true>(f, p);
   }
+  __device__ __forceinline__ static Raw unpack(__half v) { return __half2float(v); }
+  __device__ __forceinline__ static __half pack(Raw v) { return __float2half_rn(v); }
   __device__ __forceinline__ static double to_f64(__half v, int i) { return weight(i) + (double)__half2float(v); }
   __device__ __forceinline__ static __half from_f64(double f, int i) {
     // FP64 -> FP16 in one rounding (a detour through FP32 could double-round).
@@ -242,6 +250,8 @@ struct Storage<f64df> {
 #pragma unroll
     for (int i = 0; i < Q; ++i) f[i] = (f[i] + f32_to_f64(d[i].hi)) + f32_to_f64(d[i].lo);
   }
+  __device__ __forceinline__ static Raw unpack(f64df v) { return v.v; }
+  __device__ __forceinline__ static f64df pack(Raw v) { return f64df{v}; }
   __device__ __forceinline__ static double to_f64(f64df v, int) { return v.v; }
   __device__ __forceinline__ static f64df from_f64(double f, int) { return f64df{f}; }
 };
@@ -262,6 +272,8 @@ struct Storage<f32df> {
 #pragma unroll
     for (int i = 0; i < Q; ++i) f[i] = __fadd_rn(d[i].hi, d[i].lo);
   }
+  __device__ __forceinline__ static Raw unpack(f32df v) { return v.v; }
+  __device__ __forceinline__ static f32df pack(Raw v) { return f32df{v}; }
   __device__ __forceinline__ static double to_f64(f32df v, int i) { return weight(i) + (double)v.v; }
   __device__ __forceinline__ static f32df from_f64(double f, int i) { return f32df{__double2float_rn(f - weight(i))}; }
 };
@@ -288,6 +300,8 @@ struct Storage<h16sr> {
 #pragma unroll
     for (int i = 0; i < Q; ++i) f[i] = round_half_stochastic(d[i], sr_bits(w, i));
   }
+  __device__ __forceinline__ static Raw unpack(h16sr v) { return __half_as_ushort(v.v); }
+  __device__ __forceinline__ static h16sr pack(Raw v) { return h16sr{__ushort_as_half((unsigned short)v)}; }
   __device__ __forceinline__ static double to_f64(h16sr v, int i) {
     return weight(i) + ldexp((double)__half2float(v.v), -kSrScaleLog2);
   }
@@ -310,6 +324,25 @@ __device__ __forceinline__ TrtSr begin_sweep<h16sr>(const TrtSr& p) {
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) p.ctr[p.parity ^ 1] = t + 1;
   q.base = p.seed + kSplitmixGamma * (1ull + (t << 32));
   return q;
+}
+
+// The same for a launch that performs two sweeps (temporal blocking): pa for
+// sweep t, pb for sweep t + 1; the counter of the other parity receives t + 2.
+template <typename S>
+__device__ __forceinline__ void begin_two_sweeps(const typename Storage<S>::Params& p, typename Storage<S>::Params& pa,
+                                                 typename Storage<S>::Params& pb) {
+  pa = p;
+  pb = p;
+}
+template <>
+__device__ __forceinline__ void begin_two_sweeps<h16sr>(const TrtSr& p, TrtSr& pa, TrtSr& pb) {
+  pa = p;
+  pb = p;
+  const unsigned long long t = p.ctr[p.parity];
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+    p.ctr[p.parity ^ 1] = t + 2;
+  pa.base = p.seed + kSplitmixGamma * (1ull + (t << 32));
+  pb.base = p.seed + kSplitmixGamma * (1ull + ((t + 1) << 32));
 }
 
 // Equilibrium in FP64, absolute or shifted by w_i (initialisation only).

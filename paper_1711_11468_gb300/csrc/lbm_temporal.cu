@@ -1,0 +1,170 @@
+// Temporal blocking of the full-array two-grid pull sweep: two time steps per
+// pass over HBM (the paper lists temporal blocking among the optimisations its
+// kernels do not cover, Sec. 3 and Sec. 6). A step reads 19 and writes 19
+// values per cell, so one step per pass is bound by HBM at 2 x 19 x S bytes
+// per update; two steps per pass halve that.
+//
+// 2.5-D wavefront: a CTA owns an in-plane region of 32 x TY cells (one warp per
+// region row) and marches along z over a segment of planes. For every plane z
+// it first runs step A (t -> t+1, gathering from the source grid in HBM) on the
+// whole region of plane z+1, keeping the post-collision values in a ring of
+// three planes in shared memory, then step B (t+1 -> t+2) on the interior
+// 30 x (TY-2) cells of plane z, gathering from the ring, and writes them to the
+// destination grid. The ring values are rounded to the storage format exactly
+// as a one-step sweep stores them, and both steps use the one-step sweep's
+// per-node arithmetic, so the result is that of two one-step sweeps, bit for
+// bit. The region's one-cell rim and the first two planes of a segment are
+// computed twice (by neighbouring CTAs); their gathers mostly hit L2.
+#include <algorithm>
+#include <mutex>
+
+#include "lbm_internal.h"
+#include "lbm_sweep.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int kTbWidth = 32;   // region width in x
+
+__device__ __forceinline__ int wrap_mod(int a, int n) {
+  const int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+template <typename S, bool kHW>
+__global__ void __launch_bounds__(512) k_dense_pull_tb2(const S* __restrict__ src, S* __restrict__ dst,
+                                                        const uint8_t* __restrict__ flags, int nx, int ny, int nz,
+                                                        int64_t stride, int seg, ParamsT<S> lp) {
+  ParamsT<S> pa, pb;
+  begin_two_sweeps<S>(lp, pa, pb);
+  extern __shared__ __align__(16) unsigned char tb_smem[];
+  S* ring = reinterpret_cast<S*>(tb_smem);   // [3 planes][19][TY][32]
+  const int TY = blockDim.y;
+  const int rx = threadIdx.x, ry = threadIdx.y;
+  const int plane = kTbWidth * TY;
+  const int x0 = blockIdx.x * (kTbWidth - 2), y0 = blockIdx.y * (TY - 2);
+  const int gx = wrap_mod(x0 - 1 + rx, nx), gy = wrap_mod(y0 - 1 + ry, ny);
+  const int zs = blockIdx.z * seg, ze = min(zs + seg, nz);
+  const bool interior = rx >= 1 && rx <= kTbWidth - 2 && ry >= 1 && ry <= TY - 2 && x0 + rx - 1 < nx &&
+                        y0 + ry - 1 < ny;
+  auto slot = [](int z) { return (z + 3) % 3; };   // z >= -1
+  auto at = [&](int sl, int i, int dy, int dx) -> S* {
+    return ring + (size_t)(sl * Q + i) * plane + (ry + dy) * kTbWidth + (rx + dx);
+  };
+
+  // step A on this thread's region cell of plane z (z in [-1, nz], wrapped)
+  auto step_a = [&](int z) {
+    const int gz = wrap_mod(z, nz);
+    const int n = gx + nx * (gy + ny * gz);
+    const uint8_t fl = flags[n];
+    if (fl == kSolidHalfway) return;   // its ring slots are never read
+    RawT<S> f[Q];
+    pull_dense_gather<S, kHW>(src, flags, Nbr(gx, gy, gz, nx, ny, nz), n, stride, f);
+    if (fl == kSolidFullway)
+      reverse(f);
+    else
+      Storage<S>::relax(f, pa, (uint32_t)n);
+    const int sl = slot(z);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) *at(sl, i, 0, 0) = Storage<S>::pack(f[i]);
+  };
+
+  // step B on this thread's interior cell of plane z (z in [0, nz))
+  auto step_b = [&](int z) {
+    if (!interior) return;
+    const int n = gx + nx * (gy + ny * z);
+    const uint8_t fl = flags[n];
+    if (fl == kSolidHalfway) return;
+    const Nbr nb(gx, gy, z, nx, ny, nz);
+    RawT<S> f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (kHW && i != 0 && flags[n + nb.up(i)] == kSolidHalfway)
+        f[i] = Storage<S>::unpack(*at(slot(z), opp(i), 0, 0));
+      else
+        f[i] = Storage<S>::unpack(*at(slot(z - cz(i)), i, -cy(i), -cx(i)));
+    }
+    if (fl == kSolidFullway)
+      reverse(f);
+    else
+      Storage<S>::relax(f, pb, (uint32_t)n);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + n, f[i]);
+  };
+
+  // every thread runs the same loop (zs, ze are uniform), so the barriers match
+  step_a(zs - 1);
+  step_a(zs);
+  for (int z = zs; z < ze; ++z) {
+    step_a(z + 1);   // overwrites the slot of plane z - 2, last read by step B of z - 1
+    __syncthreads();
+    step_b(z);
+    __syncthreads();
+  }
+}
+
+template <typename S>
+size_t tb_smem_bytes(int ty) {
+  return (size_t)3 * Q * kTbWidth * ty * sizeof(S);
+}
+
+// Largest TY (region rows) the shared memory allows for S, at most `want`.
+template <typename S>
+int tb_rows(int want) {
+  int ty = std::max(4, std::min(16, want));
+  while (ty > 4 && tb_smem_bytes<S>(ty) > (size_t)200 * 1024) ty /= 2;
+  return ty;
+}
+
+template <typename S, bool kHW>
+cudaError_t tb_launch(const LatticeView& v, const S* src, S* dst, const ParamsT<S>& p, int threads, cudaStream_t s) {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_dense_pull_tb2<S, kHW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tb_smem_bytes<S>(tb_rows<S>(16)));
+  });
+  const int ty = tb_rows<S>(threads / kTbWidth);
+  const size_t smem = tb_smem_bytes<S>(ty);
+  const int tiles_x = (v.nx + kTbWidth - 3) / (kTbWidth - 2);
+  const int tiles_y = (v.ny + ty - 3) / (ty - 2);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_pull_tb2<S, kHW>, kTbWidth * ty, smem);
+  // enough z segments for about four waves of resident CTAs, each at least 8 planes long
+  const int64_t resident = (int64_t)std::max(1, sms) * std::max(1, per_sm);
+  const int64_t want = (4 * resident + (int64_t)tiles_x * tiles_y - 1) / ((int64_t)tiles_x * tiles_y);
+  const int segs = (int)std::max<int64_t>(1, std::min<int64_t>(want, v.nz / 8));
+  const int seg = (v.nz + segs - 1) / segs;
+  const dim3 grid((unsigned)tiles_x, (unsigned)tiles_y, (unsigned)((v.nz + seg - 1) / seg));
+  k_dense_pull_tb2<S, kHW><<<grid, dim3(kTbWidth, ty), smem, s>>>(src, dst, v.flags, v.nx, v.ny, v.nz, v.stride, seg,
+                                                                    p);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t tb_typed(const LatticeView& v, int parity, const void* src, void* dst, const TrtParams& tp, int threads,
+                     cudaStream_t s) {
+  const ParamsT<S> p = params_as<S>(tp, v, parity);
+  if (v.has_halfway)
+    return tb_launch<S, true>(v, static_cast<const S*>(src), static_cast<S*>(dst), p, threads, s);
+  return tb_launch<S, false>(v, static_cast<const S*>(src), static_cast<S*>(dst), p, threads, s);
+}
+
+}  // namespace
+
+cudaError_t launch_sweep_pull2(const LatticeView& v, int parity, const void* src, void* dst, const TrtParams& p,
+                               int threads, cudaStream_t s) {
+  if (v.indirect) return cudaErrorInvalidValue;
+  switch (v.prec) {
+    case kF64: return tb_typed<double>(v, parity, src, dst, p, threads, s);
+    case kF32: return tb_typed<float>(v, parity, src, dst, p, threads, s);
+    case kF16: return tb_typed<__half>(v, parity, src, dst, p, threads, s);
+    case kF64DF: return tb_typed<f64df>(v, parity, src, dst, p, threads, s);
+    case kF32DF: return tb_typed<f32df>(v, parity, src, dst, p, threads, s);
+    case kF16SR: return tb_typed<h16sr>(v, parity, src, dst, p, threads, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lbm

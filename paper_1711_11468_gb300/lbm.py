@@ -82,6 +82,8 @@ def load(path: str | None = None):
         "lbm_synchronize": [H],
         "lbm_set_stochastic_rounding": [H, ctypes.c_uint64, i64],
         "lbm_set_run_indexing": [H, i32],
+        "lbm_set_temporal_blocking": [H, i32],
+        "lbm_get_temporal_blocking": [H, ctypes.POINTER(i32)],
         "lbm_get_run_indexing": [H, ctypes.POINTER(i32)],
         "lbm_adjacency_bytes": [H, i32, ctypes.POINTER(i64)],
         "lbm_steps_done": [H, ctypes.POINTER(i64)],
@@ -232,6 +234,16 @@ def lbm_init_equilibrium(h: Handle, lattice: int, rho=None, u=None):
 
 def lbm_step(h: Handle, n: int):
     _check(load().lbm_step(h, int(n)))
+
+
+def lbm_set_temporal_blocking(h: Handle, steps_per_pass: int):
+    _check(load().lbm_set_temporal_blocking(h, int(steps_per_pass)))
+
+
+def lbm_get_temporal_blocking(h: Handle) -> int:
+    v = ctypes.c_int32()
+    _check(load().lbm_get_temporal_blocking(h, ctypes.byref(v)))
+    return int(v.value)
 
 
 def lbm_set_run_indexing(h: Handle, enable: bool):
