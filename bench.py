@@ -548,7 +548,7 @@ def run_gpu(args):
                                                              vs, pack, peak)
         variants["f16_list_aa_porous256"] = porous_variant(lbm, stream, lbm.LBM_F16_SHIFTED, lbm.LBM_AA_INPLACE, vs,
                                                            pack, peak)
-        variants["f32_batched_512"] = batch_variant(lbm, stream, min(args.steps, 100), peak)
+        variants["f32_batched_512"] = batch_variant(lbm, stream, min(args.steps, 500), peak)
         variants["f32_aa_geometries256"] = geometry_sweep(lbm, stream, min(args.steps, 50))
         micro = microbench(lbm, stream)
         accuracy = accuracy_poiseuille64(lbm, stream)
@@ -601,8 +601,9 @@ def run_gpu(args):
 
 
 # ------------------------------------------------------------ CPU oracle arm
-def cpu_sample(seconds: float):
-    """Oracle push steps on the duct workload until `seconds` of CPU work."""
+def cpu_sample(seconds: float, nthreads: int = 0):
+    """Oracle push steps on the duct workload until `seconds` of CPU work
+    (nthreads <= 0: every core OpenMP offers)."""
     import oracle
     oracle.build()
     flags = inputs.duct_flags(*DIMS)
@@ -614,17 +615,19 @@ def cpu_sample(seconds: float):
     steps, t = 0, 0.0
     while t < seconds or steps == 0:
         t0 = time.perf_counter()
-        oracle.step(DIMS, flags, WORKLOAD["omega"], wm, WORKLOAD["force"], f, g)
+        oracle.step(DIMS, flags, WORKLOAD["omega"], wm, WORKLOAD["force"], f, g, nthreads)
         t += time.perf_counter() - t0
         f, g = g, f
         steps += 1
-    return nf * steps / t / 1e6, steps, t, oracle.max_threads()
+    return nf * steps / t / 1e6, steps, t, nthreads if nthreads > 0 else oracle.max_threads()
 
 
 def cpu_baseline(seconds: float):
     v, steps, t, cores = cpu_sample(seconds)
+    v1, steps1, t1, _ = cpu_sample(0.0, 1)   # one step on one core
     return {"value": round(v, 2), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} oracle steps of the 256^3 duct ({t:.1f} s, FP64 push, OpenMP)"}
+            "sample": f"{steps} oracle steps of the 256^3 duct ({t:.1f} s, FP64 push, OpenMP)",
+            "value_1thread": round(v1, 3), "sample_1thread": f"{steps1} oracle step on 1 core ({t1:.1f} s)"}
 
 
 def run_reference(args):
