@@ -33,13 +33,13 @@ from paper_1711_11468_gb300 import inputs  # noqa: E402
 WORKLOAD = inputs.DUCT_256
 DIMS = WORKLOAD["dims"]
 # FP64 pipe instructions per fluid lattice update of the FP64 AA sweep, from
-# ncu per-opcode counters (DADD 69, DFMA 45, DMUL 17 per fluid cell; see
+# ncu per-opcode counters (DADD 63, DFMA 45, DMUL 16 per fluid cell; see
 # profiles/dense_aa_f64_duct128_ncu.md), the FP64 pipe's rate on GB300 (2 per
 # clock per SM at 2.07 GHz), and the DRAM bytes one launch of that sweep moves
-# on the 256^3 duct (dram__bytes_read + write, profiles/dense_aa_duct256_dram_traffic.md).
-FP64_INSTR_PER_FLUP = 131.0
+# on the 256^3 duct (dram__bytes_read + write, profiles/dense_aa_f64_duct256_launch_list.md).
+FP64_INSTR_PER_FLUP = 124.0
 FP64_INSTR_PER_SEC = 152 * 2 * 2.07e9
-F64_AA_TRAFFIC_PER_LAUNCH = 2.53e9 + 2.45e9
+F64_AA_TRAFFIC_PER_LAUNCH = 2.527e9 + 2.448e9
 
 METRIC = "MFLUP/s and % of HBM roofline, FP64 vs FP32/FP16-shifted vs batched, at stated error"
 UNIT = "MFLUP/s"
@@ -559,7 +559,8 @@ def run_gpu(args):
     alu_achieved = value / world * 1e6 * FP64_INSTR_PER_FLUP
     alu = {"bound": "alu", "achieved": round(alu_achieved / 1e9, 1), "peak": round(fp64_rate / 1e9, 1),
            "unit": "G FP64 instr/s", "frac": round(alu_achieved / fp64_rate, 4),
-           "traffic": F64_AA_TRAFFIC_PER_LAUNCH, "traffic_per_fluid_cell": round(F64_AA_TRAFFIC_PER_LAUNCH / nf, 1),
+           "traffic": F64_AA_TRAFFIC_PER_LAUNCH,
+           "traffic_per_fluid_cell": (round(F64_AA_TRAFFIC_PER_LAUNCH / nf, 1) if F64_AA_TRAFFIC_PER_LAUNCH else None),
            "instr_per_flup": FP64_INSTR_PER_FLUP,
            "peak_source": "152 SMs x 2 FP64 FMA/clock x 2.07 GHz (FMA probe measured 598 G/s)"}
     roofline = alu if alu["frac"] > achieved / peak else {
