@@ -70,6 +70,13 @@ def test_argument_validation_without_gpu(lib):
     assert lib.lbm_read_pdfs(None, 0, None, 0) == lbm.LBM_ERR_ARG
     assert lib.lbm_set_allocator(lbm.ALLOC_FN(lambda n, c: 0), lbm.FREE_FN(), None) == lbm.LBM_ERR_ARG
     assert lib.lbm_bench_copy19(None, None, 10, 10, 8, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_set_stochastic_rounding(None, 1, 0) == lbm.LBM_ERR_ARG
+    assert lib.lbm_set_run_indexing(None, 1) == lbm.LBM_ERR_ARG
+    assert lib.lbm_set_temporal_blocking(None, 2) == lbm.LBM_ERR_ARG
+    out = (ctypes.c_int64 * 2)()
+    assert lib.lbm_adjacency_bytes(None, 0, out) == lbm.LBM_ERR_ARG
+    d = lbm.make_desc((8, 8, 8), precision=6)
+    assert lib.lbm_create_lattice(ctypes.byref(d), None, ctypes.byref(h)) == lbm.LBM_ERR_ARG
 
 
 def test_desc_layout_matches_header():
