@@ -302,10 +302,17 @@ int lbm_read_adjacency(lbm_handle h, int32_t lattice, int32_t* out, size_t out_l
  * times candidate shapes for `steps` steps each on the handle's own data (the
  * state is saved and restored around the trials) and keeps the fastest. The
  * launch-shape search is the GPU analogue of the paper's search over blocking
- * factors (Sec. 4.2, Sec. 4.3). */
+ * factors (Sec. 4.2, Sec. 4.3). The choice (shape, link encoding, steps per
+ * pass) is cached for the process, keyed by a signature of the handle: device,
+ * precision, propagation, and per lattice its dims, addressing, fluid count and
+ * bounce-back kinds; a later lbm_autotune on a handle with the same signature
+ * applies the cached choice without trials. lbm_autotune_cache returns
+ * {entries, hits since the process started}; lbm_autotune_clear empties it. */
 int lbm_set_tuning(lbm_handle h, int32_t threads, int32_t cells_per_thread, int32_t ctas_per_sm);
 int lbm_get_tuning(lbm_handle h, int32_t out[3]);
 int lbm_autotune(lbm_handle h, int32_t steps);
+int lbm_autotune_cache(int64_t out[2]);
+int lbm_autotune_clear(void);
 
 /* Device bytes the handle holds (flags, PDF storage, fluid and adjacency
  * lists, batch tables). */

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -403,6 +404,30 @@ int ready_to_step(lbm_handle h) {
       return fail(LBM_ERR_STATE, "lattice " + std::to_string(k) + " needs geometry, params and an initial state");
   }
   return LBM_OK;
+}
+
+// Autotuner results for the process, keyed by tune_signature().
+struct TuneChoice {
+  int threads, cells_per_thread, ctas_per_sm;
+  bool run_indexing;
+  int steps_per_pass;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune_cache;
+int64_t g_tune_hits = 0;
+
+// What the fastest launch shape depends on: the device, the storage format and
+// propagation, and each lattice's size, addressing, fluid count and bounce-back kinds.
+std::string tune_signature(lbm_handle h) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::string sig = "dev" + std::to_string(dev) + "/p" + std::to_string(h->prec) + "/g" + std::to_string(h->prop) +
+                    "/n" + std::to_string(h->lat.size());
+  for (const Lattice& L : h->lat)
+    sig += "/" + std::to_string(L.desc.nx) + "x" + std::to_string(L.desc.ny) + "x" + std::to_string(L.desc.nz) +
+           (L.indirect() ? "i" : "d") + std::to_string(L.nf) + (L.has_fullway ? "F" : "") +
+           (L.has_halfway ? "H" : "");
+  return sig;
 }
 
 int sm_count() {
@@ -899,10 +924,39 @@ int lbm_get_tuning(lbm_handle h, int32_t out[3]) {
   return LBM_OK;
 }
 
+int lbm_autotune_cache(int64_t out[2]) {
+  if (!out) return fail(LBM_ERR_ARG, "null output");
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  out[0] = (int64_t)g_tune_cache.size();
+  out[1] = g_tune_hits;
+  return LBM_OK;
+}
+
+int lbm_autotune_clear(void) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache.clear();
+  return LBM_OK;
+}
+
 int lbm_autotune(lbm_handle h, int32_t steps) {
   if (int rc = check_handle(h)) return rc;
   if (steps < 2) return fail(LBM_ERR_ARG, "steps must be >= 2");
   if (int rc = ready_to_step(h)) return rc;
+  const std::string sig = tune_signature(h);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(sig);
+    if (it != g_tune_cache.end()) {
+      ++g_tune_hits;
+      h->drop_graphs();
+      h->threads = it->second.threads;
+      h->cells_per_thread = it->second.cells_per_thread;
+      h->ctas_per_sm = it->second.ctas_per_sm;
+      h->run_indexing = it->second.run_indexing;
+      h->steps_per_pass = it->second.steps_per_pass;
+      return LBM_OK;
+    }
+  }
   steps += steps & 1;   // even: the AA parity and the pull buffers come back
   // save every lattice's state so the trials leave no trace
   std::vector<void*> saved(h->lat.size(), nullptr);
@@ -988,6 +1042,11 @@ int lbm_autotune(lbm_handle h, int32_t steps) {
   LBM_CUDA(h, cudaStreamSynchronize(h->stream), "autotune sync");
   for (size_t k = 0; k < h->lat.size(); ++k) h->dfree(saved[k], pdf_bytes(h->lat[k], h->prec));
   if (h->poisoned) return fail(LBM_ERR_CUDA, "autotune hit a CUDA error");
+  if (rc == LBM_OK) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[sig] = TuneChoice{h->threads, h->cells_per_thread, h->ctas_per_sm, h->run_indexing,
+                                   h->steps_per_pass};
+  }
   return rc;
 }
 

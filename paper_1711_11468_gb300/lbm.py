@@ -82,6 +82,8 @@ def load(path: str | None = None):
         "lbm_synchronize": [H],
         "lbm_set_stochastic_rounding": [H, ctypes.c_uint64, i64],
         "lbm_set_run_indexing": [H, i32],
+        "lbm_autotune_cache": [ctypes.POINTER(i64)],
+        "lbm_autotune_clear": [],
         "lbm_set_temporal_blocking": [H, i32],
         "lbm_get_temporal_blocking": [H, ctypes.POINTER(i32)],
         "lbm_get_run_indexing": [H, ctypes.POINTER(i32)],
@@ -349,6 +351,17 @@ def lbm_get_tuning(h: Handle):
 
 def lbm_autotune(h: Handle, steps: int = 10):
     _check(load().lbm_autotune(h, steps))
+
+
+def lbm_autotune_cache():
+    """(entries, hits) of the process-wide autotuning cache."""
+    out = (ctypes.c_int64 * 2)()
+    _check(load().lbm_autotune_cache(out))
+    return int(out[0]), int(out[1])
+
+
+def lbm_autotune_clear():
+    _check(load().lbm_autotune_clear())
 
 
 def lbm_memory_bytes(h: Handle) -> int:

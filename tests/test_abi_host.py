@@ -79,6 +79,14 @@ def test_argument_validation_without_gpu(lib):
     assert lib.lbm_create_lattice(ctypes.byref(d), None, ctypes.byref(h)) == lbm.LBM_ERR_ARG
 
 
+def test_autotune_cache_host_calls(lib):
+    from paper_1711_11468_gb300 import lbm
+    assert lib.lbm_autotune_cache(None) == lbm.LBM_ERR_ARG
+    lbm.lbm_autotune_clear()
+    entries, hits = lbm.lbm_autotune_cache()
+    assert entries == 0 and hits >= 0
+
+
 def test_desc_layout_matches_header():
     from paper_1711_11468_gb300 import lbm
     assert ctypes.sizeof(lbm.lbm_desc) == 28

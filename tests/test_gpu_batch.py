@@ -120,3 +120,37 @@ def test_autotune_leaves_state_untouched(lbm):
         lbm.lbm_step(h, 3)
     finally:
         lbm.lbm_destroy(h)
+
+
+def test_autotune_cache_reuses_the_choice_for_the_same_signature(lbm):
+    """A second handle with the same signature takes the cached shape without
+    trials; another signature is tuned afresh."""
+    import torch
+    lbm.lbm_autotune_clear()
+    fl = inputs.duct_flags(48, 24, 24)
+
+    def make(dims, flags):
+        h = lbm.lbm_create_lattice(lbm.make_desc(dims, lbm.LBM_F32_SHIFTED, 0, 1, (1, 0, 0)),
+                                   torch.cuda.current_stream())
+        lbm.lbm_set_geometry(h, 0, flags)
+        lbm.lbm_set_params(h, 0, 1.0, 3 / 16, (0, 0, 0))
+        lbm.lbm_init_equilibrium(h, 0)
+        return h
+
+    a, b = make((48, 24, 24), fl), make((48, 24, 24), fl)
+    c = make((40, 24, 24), inputs.duct_flags(40, 24, 24))
+    try:
+        lbm.lbm_autotune(a, 4)
+        e0, h0 = lbm.lbm_autotune_cache()
+        assert e0 == 1
+        lbm.lbm_set_tuning(b, 64, 1, 0)
+        lbm.lbm_autotune(b, 4)
+        e1, h1 = lbm.lbm_autotune_cache()
+        assert (e1, h1) == (1, h0 + 1)
+        assert lbm.lbm_get_tuning(b) == lbm.lbm_get_tuning(a)
+        lbm.lbm_autotune(c, 4)
+        e2, h2 = lbm.lbm_autotune_cache()
+        assert (e2, h2) == (2, h1)
+    finally:
+        for h in (a, b, c):
+            lbm.lbm_destroy(h)
