@@ -390,6 +390,19 @@ def microbench(lbm, stream, elem: int = 8, n: int = 1 << 24, reps: int = 5):
             best = min(best, e0.elapsed_time(e1) / 1e3)
         out[name + "_gbs"] = round(2 * 19 * n * elem / best / 1e9, 1)
     del a, b
+    # FP64 pipe: 8 chains of FMAs per thread, 8 CTAs of 256 per SM
+    blocks, iters = torch.cuda.get_device_properties(0).multi_processor_count * 8, 4096
+    buf = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    best = 1e30
+    for _ in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lbm.lbm_bench_fma64(buf.data_ptr(), blocks, iters, stream)
+        e1.record(stream)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    out["fp64_fma_per_s_g"] = round(8 * iters * blocks * 256 / best / 1e9, 1)
+    del buf
     return out
 
 

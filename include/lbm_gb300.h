@@ -307,12 +307,20 @@ int lbm_read_adjacency(lbm_handle h, int32_t lattice, int32_t* out, size_t out_l
  * precision, propagation, and per lattice its dims, addressing, fluid count and
  * bounce-back kinds; a later lbm_autotune on a handle with the same signature
  * applies the cached choice without trials. lbm_autotune_cache returns
- * {entries, hits since the process started}; lbm_autotune_clear empties it. */
+ * {entries, hits since the process started}; lbm_autotune_clear empties it;
+ * lbm_autotune_save writes it to a text file (one line per signature: the
+ * signature, threads, cells_per_thread, ctas_per_sm, run_indexing,
+ * steps_per_pass) and lbm_autotune_load merges such a file into it
+ * (LBM_ERR_ARG if the file cannot be read or written, or on a malformed line,
+ * in which case nothing is merged). The signature starts with the GPU's name
+ * and SM count. */
 int lbm_set_tuning(lbm_handle h, int32_t threads, int32_t cells_per_thread, int32_t ctas_per_sm);
 int lbm_get_tuning(lbm_handle h, int32_t out[3]);
 int lbm_autotune(lbm_handle h, int32_t steps);
 int lbm_autotune_cache(int64_t out[2]);
 int lbm_autotune_clear(void);
+int lbm_autotune_save(const char* path);
+int lbm_autotune_load(const char* path);
 
 /* Device bytes the handle holds (flags, PDF storage, fluid and adjacency
  * lists, batch tables). */
@@ -338,6 +346,14 @@ const char* lbm_last_error(void);
 int lbm_bench_copy19(const void* src, void* dst, int64_t n, int64_t stride_elems, int32_t elem_bytes,
                      void* cuda_stream);
 int lbm_bench_update19(void* buf, int64_t n, int64_t stride_elems, int32_t elem_bytes, void* cuda_stream);
+
+/* FP64 fused multiply-add throughput probe (the bound of the FP64 sweep on
+ * this GPU): `blocks` CTAs of 256 threads each run 8 independent chains of
+ * `iterations` FMAs and write their sums to out (device, blocks * 256 doubles,
+ * caller-owned). Asynchronous on cuda_stream; the caller times it
+ * (2 * 8 * iterations * blocks * 256 flops). LBM_ERR_ARG for NULL or
+ * non-positive sizes. */
+int lbm_bench_fma64(double* out, int32_t blocks, int32_t iterations, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -381,6 +381,17 @@ int finish_geometry(lbm_handle h, Lattice& L) {
     LBM_CUDA(h, cudaMemcpyAsync(&nf_check, nfbuf.p, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream), "copy nf");
     LBM_CUDA(h, cudaStreamSynchronize(h->stream), "adjacency sync");
     if (nf_check != L.nf) return fail(LBM_ERR_STATE, "fluid compaction disagrees with the flag count");
+    // every link addresses an element of the 19 direction arrays
+    Scratch badbuf(h, sizeof(unsigned long long));
+    if (!badbuf.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
+    LBM_CUDA(h, cudaMemsetAsync(badbuf.p, 0, sizeof(unsigned long long), h->stream), "memset");
+    LBM_CUDA(h, launch_links_check(L.view(), (uint64_t)Q * (uint64_t)L.stride, badbuf.as<unsigned long long>(),
+                                   h->stream),
+             "link check");
+    unsigned long long bad = 1;
+    LBM_CUDA(h, cudaMemcpyAsync(&bad, badbuf.p, sizeof(bad), cudaMemcpyDeviceToHost, h->stream), "copy link check");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "link check sync");
+    if (bad != 0) return fail(LBM_ERR_STATE, "adjacency list holds offsets outside the PDF arrays");
     if (int rc = build_run_index(h, L)) return rc;
   }
   L.geometry = true;
@@ -421,8 +432,12 @@ int64_t g_tune_hits = 0;
 std::string tune_signature(lbm_handle h) {
   int dev = 0;
   cudaGetDevice(&dev);
-  std::string sig = "dev" + std::to_string(dev) + "/p" + std::to_string(h->prec) + "/g" + std::to_string(h->prop) +
-                    "/n" + std::to_string(h->lat.size());
+  cudaDeviceProp prop{};
+  std::string gpu = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? std::string(prop.name) : "gpu";
+  for (char& ch : gpu)
+    if (ch == ' ' || ch == '/' || ch == '\t') ch = '_';
+  std::string sig = gpu + "/sm" + std::to_string(prop.multiProcessorCount) + "/p" + std::to_string(h->prec) + "/g" +
+                    std::to_string(h->prop) + "/n" + std::to_string(h->lat.size());
   for (const Lattice& L : h->lat)
     sig += "/" + std::to_string(L.desc.nx) + "x" + std::to_string(L.desc.ny) + "x" + std::to_string(L.desc.nz) +
            (L.indirect() ? "i" : "d") + std::to_string(L.nf) + (L.has_fullway ? "F" : "") +
@@ -938,6 +953,46 @@ int lbm_autotune_clear(void) {
   return LBM_OK;
 }
 
+int lbm_autotune_save(const char* path) {
+  if (!path) return fail(LBM_ERR_ARG, "null path");
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  FILE* fp = std::fopen(path, "w");
+  if (!fp) return fail(LBM_ERR_ARG, std::string("cannot write ") + path);
+  std::fprintf(fp, "# lbm_gb300 autotune cache: signature threads cells_per_thread ctas_per_sm run_indexing "
+                   "steps_per_pass\n");
+  for (const auto& kv : g_tune_cache)
+    std::fprintf(fp, "%s %d %d %d %d %d\n", kv.first.c_str(), kv.second.threads, kv.second.cells_per_thread,
+                 kv.second.ctas_per_sm, kv.second.run_indexing ? 1 : 0, kv.second.steps_per_pass);
+  const bool ok = std::fclose(fp) == 0;
+  return ok ? LBM_OK : fail(LBM_ERR_ARG, std::string("cannot write ") + path);
+}
+
+int lbm_autotune_load(const char* path) {
+  if (!path) return fail(LBM_ERR_ARG, "null path");
+  FILE* fp = std::fopen(path, "r");
+  if (!fp) return fail(LBM_ERR_ARG, std::string("cannot read ") + path);
+  std::map<std::string, TuneChoice> read;
+  char line[8192];
+  int lineno = 0;
+  while (std::fgets(line, sizeof(line), fp)) {
+    ++lineno;
+    if (line[0] == '#' || line[0] == '\n') continue;
+    char sig[8192];
+    int t = 0, c = 0, g = 0, r = 0, spp = 0;
+    if (std::sscanf(line, "%8191s %d %d %d %d %d", sig, &t, &c, &g, &r, &spp) != 6 || t < 32 || t > 512 ||
+        t % 32 != 0 || (c != 1 && c != 2 && c != 4 && c != 8) || g < 0 || g > 64 || (r != 0 && r != 1) ||
+        (spp != 1 && spp != 2)) {
+      std::fclose(fp);
+      return fail(LBM_ERR_ARG, std::string(path) + ": malformed line " + std::to_string(lineno));
+    }
+    read[sig] = TuneChoice{t, c, g, r == 1, spp};
+  }
+  std::fclose(fp);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (const auto& kv : read) g_tune_cache[kv.first] = kv.second;
+  return LBM_OK;
+}
+
 int lbm_autotune(lbm_handle h, int32_t steps) {
   if (int rc = check_handle(h)) return rc;
   if (steps < 2) return fail(LBM_ERR_ARG, "steps must be >= 2");
@@ -1071,6 +1126,13 @@ int lbm_selftest_bounded_wait(lbm_handle h, int32_t polls) {
   LBM_CUDA(h, launch_wait_selftest((uint32_t)polls, h->d_status, h->stream), "wait self-test");
   LBM_CUDA(h, cudaStreamSynchronize(h->stream), "wait self-test sync");
   return check_device_status(h);
+}
+
+int lbm_bench_fma64(double* out, int32_t blocks, int32_t iterations, void* cuda_stream) {
+  if (!out || blocks < 1 || iterations < 1) return fail(LBM_ERR_ARG, "bad fma64 arguments");
+  cudaError_t e = launch_fma64(out, blocks, iterations, static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("fma64: ") + cudaGetErrorString(e));
+  return LBM_OK;
 }
 
 int lbm_bench_update19(void* buf, int64_t n, int64_t stride_elems, int32_t elem_bytes, void* cuda_stream) {

@@ -2,6 +2,7 @@
 // arrays concurrently (19 read and 19 write streams), update-19 updates 19
 // arrays in place. They give the "adjusted" roofline bandwidth for the two-grid
 // and the in-place sweeps. Bitwise integer work so any element size is valid.
+// fma64 measures the FP64 pipe, the bound of the FP64 sweep on this GPU.
 #include "lbm_async.cuh"
 #include "lbm_internal.h"
 
@@ -46,6 +47,23 @@ __global__ void k_wait_selftest(uint32_t polls, int* status) {
   if (!mbar_wait_bounded(&bar, 0, polls) && threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
 }
 
+// FP64 pipe throughput: eight independent chains of fused multiply-adds per
+// thread (each 2 flops); the sums go to out[] so nothing is optimised away.
+__global__ void __launch_bounds__(256) k_fma64(double* __restrict__ out, int iterations) {
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+  const double b = 0.9999999, c = 1e-7;
+  for (int it = 0; it < iterations; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sum += a[k];
+  out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
 unsigned grid_for(int64_t n) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -65,6 +83,11 @@ cudaError_t launch_copy19(const void* src, void* dst, int64_t n, int64_t stride,
     case 2: k_copy19<unsigned short><<<g, 256, 0, s>>>((const unsigned short*)src, (unsigned short*)dst, n, stride); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fma64(double* out, int blocks, int iterations, cudaStream_t s) {
+  k_fma64<<<blocks, 256, 0, s>>>(out, iterations);
   return cudaGetLastError();
 }
 

@@ -158,6 +158,17 @@ __global__ void k_links(int nx, int ny, int nz, int64_t nf, int64_t stride, cons
   }
 }
 
+// Every link must address an element of the 19 direction arrays.
+__global__ void k_links_check(const uint32_t* __restrict__ link, int64_t nf, int64_t stride, uint64_t limit,
+                              unsigned long long* __restrict__ bad) {
+  unsigned long long c = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 18 * nf; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / nf, k = t - i * nf;
+    c += (uint64_t)link[i * stride + k] >= limit;
+  }
+  if (c) atomicAdd(bad, c);
+}
+
 // Fluid cells on each boundary face: out[2a] on the low face of axis a, out[2a+1] on the high one.
 __global__ void k_face_fluid(const uint8_t* __restrict__ flags, int nx, int ny, int nz,
                              unsigned long long* __restrict__ out) {
@@ -217,6 +228,13 @@ cudaError_t launch_links(const LatticeView& v, const int32_t* d_list_index, bool
   if (v.n_nodes == 0) return cudaSuccess;
   k_links<<<(unsigned)((v.n_nodes + 255) / 256), 256, 0, s>>>(v.nx, v.ny, v.nz, v.n_nodes, v.stride, v.cell_of,
                                                              d_list_index, aa, d_link);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_links_check(const LatticeView& v, uint64_t limit, unsigned long long* d_bad, cudaStream_t s) {
+  if (v.n_nodes == 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((18 * v.n_nodes + 255) / 256, 4096);
+  k_links_check<<<(unsigned)blocks, 256, 0, s>>>(v.link, v.n_nodes, v.stride, limit, d_bad);
   return cudaGetLastError();
 }
 

@@ -146,12 +146,17 @@ cudaError_t launch_links(const LatticeView& v, const int32_t* d_list_index, bool
 // caller): out[2a] on the low face of axis a, out[2a+1] on the high face.
 cudaError_t launch_face_fluid(const uint8_t* d_flags, int nx, int ny, int nz, unsigned long long* d_out,
                               cudaStream_t s);
+// Count link-table entries outside [0, limit) into *d_bad (zeroed by the caller).
+cudaError_t launch_links_check(const LatticeView& v, uint64_t limit, unsigned long long* d_bad, cudaStream_t s);
 // Count flags into out[4] (zeroed by the caller): cells with flag 0, 1, 2, other.
 cudaError_t launch_count_flags(const uint8_t* d_flags, int64_t n, unsigned long long* d_out, cudaStream_t s);
 
 // ---------------------------------------------------------- micro-benchmarks
 cudaError_t launch_copy19(const void* src, void* dst, int64_t n, int64_t stride, int elem, cudaStream_t s);
 cudaError_t launch_update19(void* buf, int64_t n, int64_t stride, int elem, cudaStream_t s);
+// FP64 fused multiply-add throughput: blocks x 256 threads, 8 x iterations FMAs
+// each; out[blocks * 256] receives the sums.
+cudaError_t launch_fma64(double* out, int blocks, int iterations, cudaStream_t s);
 // Bounded-wait self-test: sets the timeout bit of *status after `polls` polls.
 cudaError_t launch_wait_selftest(uint32_t polls, int* status, cudaStream_t s);
 

@@ -84,6 +84,9 @@ def load(path: str | None = None):
         "lbm_set_run_indexing": [H, i32],
         "lbm_autotune_cache": [ctypes.POINTER(i64)],
         "lbm_autotune_clear": [],
+        "lbm_autotune_save": [ctypes.c_char_p],
+        "lbm_autotune_load": [ctypes.c_char_p],
+        "lbm_bench_fma64": [vp, i32, i32, vp],
         "lbm_set_temporal_blocking": [H, i32],
         "lbm_get_temporal_blocking": [H, ctypes.POINTER(i32)],
         "lbm_get_run_indexing": [H, ctypes.POINTER(i32)],
@@ -364,6 +367,14 @@ def lbm_autotune_clear():
     _check(load().lbm_autotune_clear())
 
 
+def lbm_autotune_save(path: str):
+    _check(load().lbm_autotune_save(os.fsencode(path)))
+
+
+def lbm_autotune_load(path: str):
+    _check(load().lbm_autotune_load(os.fsencode(path)))
+
+
 def lbm_memory_bytes(h: Handle) -> int:
     b = ctypes.c_int64()
     _check(load().lbm_memory_bytes(h, ctypes.byref(b)))
@@ -383,6 +394,10 @@ def lbm_selftest_bounded_wait(h: Handle, polls: int = 1000):
 def lbm_bench_copy19(src_ptr: int, dst_ptr: int, n: int, stride: int, elem_bytes: int, stream=None):
     _check(load().lbm_bench_copy19(ctypes.c_void_p(src_ptr), ctypes.c_void_p(dst_ptr), n, stride, elem_bytes,
                                    _stream_ptr(stream)))
+
+
+def lbm_bench_fma64(out_ptr: int, blocks: int, iterations: int, stream=None):
+    _check(load().lbm_bench_fma64(ctypes.c_void_p(out_ptr), int(blocks), int(iterations), _stream_ptr(stream)))
 
 
 def lbm_bench_update19(buf_ptr: int, n: int, stride: int, elem_bytes: int, stream=None):
