@@ -390,8 +390,8 @@ def microbench(lbm, stream, elem: int = 8, n: int = 1 << 24, reps: int = 5):
             best = min(best, e0.elapsed_time(e1) / 1e3)
         out[name + "_gbs"] = round(2 * 19 * n * elem / best / 1e9, 1)
     del a, b
-    # FP64 pipe: 8 chains of FMAs per thread, 8 CTAs of 256 per SM
-    blocks, iters = torch.cuda.get_device_properties(0).multi_processor_count * 8, 4096
+    # FP64 pipe: 16 chains of FMAs per thread, 8 CTAs of 256 per SM
+    blocks, iters = torch.cuda.get_device_properties(0).multi_processor_count * 8, 2048
     buf = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
     best = 1e30
     for _ in range(reps + 1):
@@ -401,7 +401,7 @@ def microbench(lbm, stream, elem: int = 8, n: int = 1 << 24, reps: int = 5):
         e1.record(stream)
         e1.synchronize()
         best = min(best, e0.elapsed_time(e1) / 1e3)
-    out["fp64_fma_per_s_g"] = round(8 * iters * blocks * 256 / best / 1e9, 1)
+    out["fp64_fma_per_s_g"] = round(16 * iters * blocks * 256 / best / 1e9, 1)
     del buf
     return out
 
@@ -441,6 +441,14 @@ def run_sweep_only(args):
     if args.workload == "duct":
         h, flags = make_duct(lbm, stream, prec, prop)
         nf = int(np.count_nonzero(flags == 0))
+    elif args.workload == "channel":
+        c = inputs.CHANNEL_384 if DIMS[0] >= 384 else inputs.POISEUILLE_64
+        flags = inputs.channel_flags(*DIMS)
+        h = lbm.lbm_create_lattice(lbm.make_desc(DIMS, prec, lbm.LBM_DIRECT, prop, (1, 0, 1)), stream)
+        lbm.lbm_set_geometry(h, 0, flags)
+        lbm.lbm_set_params(h, 0, c["omega"], c["Lambda"], c["force"])
+        lbm.lbm_init_equilibrium(h, 0)
+        nf = int(np.count_nonzero(flags == 0))
     elif args.workload == "porous":
         c = inputs.POROUS_256
         pack = inputs.sphere_pack(DIMS, c["seed"], c["r_min"], c["r_max"], c["porosity"])
@@ -472,7 +480,7 @@ def run_sweep_only(args):
     lbm.lbm_step(h, args.warmup)
     sec = time_steps(lbm, h, args.steps, stream)
     lbm.lbm_destroy(h)
-    print(json.dumps({"mode": "sweep-only", "workload": args.workload, "dims": list(DIMS),
+    print(json.dumps({"mode": "sweep-only", "config": args.config, "workload": args.workload, "dims": list(DIMS),
                       "precision": args.precision, "prop": args.prop, "steps": args.steps,
                       "mflups": round(nf * args.steps / sec / 1e6, 1)}), flush=True)
 
@@ -575,7 +583,7 @@ def run_gpu(args):
            "traffic": F64_AA_TRAFFIC_PER_LAUNCH,
            "traffic_per_fluid_cell": (round(F64_AA_TRAFFIC_PER_LAUNCH / nf, 1) if F64_AA_TRAFFIC_PER_LAUNCH else None),
            "instr_per_flup": FP64_INSTR_PER_FLUP,
-           "peak_source": "152 SMs x 2 FP64 FMA/clock x 2.07 GHz (FMA probe measured 598 G/s)"}
+           "peak_source": "152 SMs x 2 FP64 FMA/clock x 2.07 GHz (nominal; live probe: microbench fp64_fma_per_s_g)"}
     roofline = alu if alu["frac"] > achieved / peak else {
         "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
         "frac": round(achieved / peak, 4), "traffic": None, "bytes_per_flup": bpf, "peak_source": peak_kind}
@@ -674,8 +682,12 @@ def main():
     ap.add_argument("--precision", default="f64", choices=["f64", "f32", "f16", "f64df", "f32df", "f16sr"],
                     help="profiling (with --sweep-only)")
     ap.add_argument("--prop", default="aa", choices=["aa", "pull"], help="profiling (with --sweep-only)")
-    ap.add_argument("--workload", default="duct", choices=["duct", "porous", "batch"],
+    ap.add_argument("--workload", default="duct", choices=["duct", "channel", "porous", "batch"],
                     help="profiling (with --sweep-only)")
+    ap.add_argument("--config", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4],
+                    help="profiling (with --sweep-only): the five workloads - 0 Poiseuille channel 64^3 FP64, "
+                         "1 duct 256^3 FP64, 2 porous 256^3 FP64 fluid list, 3 channel 384^3 (--precision), "
+                         "4 batch of 512 FP32 lattices")
     ap.add_argument("--batch-count", type=int, default=512, help="profiling: lattices in the batch workload")
     ap.add_argument("--tuning", default="", help="profiling: threads,cells_per_thread,ctas_per_sm")
     ap.add_argument("--steps-per-pass", type=int, default=0, choices=[0, 1, 2],
@@ -683,6 +695,13 @@ def main():
     ap.add_argument("--run-indexing", default="", choices=["", "on", "off"],
                     help="profiling: fluid lists read the run-indexed links (on) or the link table (off)")
     args = ap.parse_args()
+    if args.config >= 0:
+        args.sweep_only = True
+        workload, dims, precision = {0: ("channel", 64, "f64"), 1: ("duct", 256, "f64"), 2: ("porous", 256, "f64"),
+                                     3: ("channel", 384, args.precision), 4: ("batch", 0, "f32")}[args.config]
+        args.workload = workload
+        args.dims = dims
+        args.precision = precision
     if args.dims:
         global DIMS
         DIMS = (args.dims, args.dims, args.dims)

@@ -348,10 +348,10 @@ int lbm_bench_copy19(const void* src, void* dst, int64_t n, int64_t stride_elems
 int lbm_bench_update19(void* buf, int64_t n, int64_t stride_elems, int32_t elem_bytes, void* cuda_stream);
 
 /* FP64 fused multiply-add throughput probe (the bound of the FP64 sweep on
- * this GPU): `blocks` CTAs of 256 threads each run 8 independent chains of
+ * this GPU): `blocks` CTAs of 256 threads each run 16 independent chains of
  * `iterations` FMAs and write their sums to out (device, blocks * 256 doubles,
  * caller-owned). Asynchronous on cuda_stream; the caller times it
- * (2 * 8 * iterations * blocks * 256 flops). LBM_ERR_ARG for NULL or
+ * (2 * 16 * iterations * blocks * 256 flops). LBM_ERR_ARG for NULL or
  * non-positive sizes. */
 int lbm_bench_fma64(double* out, int32_t blocks, int32_t iterations, void* cuda_stream);
 

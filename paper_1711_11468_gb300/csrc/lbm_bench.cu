@@ -47,20 +47,20 @@ __global__ void k_wait_selftest(uint32_t polls, int* status) {
   if (!mbar_wait_bounded(&bar, 0, polls) && threadIdx.x == 0) atomicOr(status, kStatusWaitTimeout);
 }
 
-// FP64 pipe throughput: eight independent chains of fused multiply-adds per
+// FP64 pipe throughput: sixteen independent chains of fused multiply-adds per
 // thread (each 2 flops); the sums go to out[] so nothing is optimised away.
 __global__ void __launch_bounds__(256) k_fma64(double* __restrict__ out, int iterations) {
-  double a[8];
+  double a[16];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) a[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+  for (int k = 0; k < 16; ++k) a[k] = 1.0 + 1e-3 * (threadIdx.x + k);
   const double b = 0.9999999, c = 1e-7;
   for (int it = 0; it < iterations; ++it) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+    for (int k = 0; k < 16; ++k) a[k] = fma(a[k], b, c);
   }
   double sum = 0.0;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) sum += a[k];
+  for (int k = 0; k < 16; ++k) sum += a[k];
   out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = sum;
 }
 

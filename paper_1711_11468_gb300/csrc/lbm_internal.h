@@ -154,7 +154,7 @@ cudaError_t launch_count_flags(const uint8_t* d_flags, int64_t n, unsigned long 
 // ---------------------------------------------------------- micro-benchmarks
 cudaError_t launch_copy19(const void* src, void* dst, int64_t n, int64_t stride, int elem, cudaStream_t s);
 cudaError_t launch_update19(void* buf, int64_t n, int64_t stride, int elem, cudaStream_t s);
-// FP64 fused multiply-add throughput: blocks x 256 threads, 8 x iterations FMAs
+// FP64 fused multiply-add throughput: blocks x 256 threads, 16 x iterations FMAs
 // each; out[blocks * 256] receives the sums.
 cudaError_t launch_fma64(double* out, int blocks, int iterations, cudaStream_t s);
 // Bounded-wait self-test: sets the timeout bit of *status after `polls` polls.
