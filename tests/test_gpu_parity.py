@@ -342,8 +342,11 @@ def test_bounded_wait_timeout_is_reported(lbm):
 
 
 @pytest.mark.parametrize("halfway", [True, False])
-@pytest.mark.parametrize("nx", [45, 46])     # odd: a lone last cell; even: the vector-access kernels
-@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4])
+# odd: a lone last cell; even: the vector-access kernels, whose x-shifted
+# directions trade values between lanes (130 and 200: several warps per row,
+# the last one partly filled, and warp edges inside the row)
+@pytest.mark.parametrize("nx", [45, 46, 130, 200])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("prop", [0, 1])
 def test_two_cells_per_thread_bitwise(lbm, orc, prec, prop, nx, halfway):
     """Two cells of a row per thread changes the schedule, not the arithmetic
@@ -356,7 +359,7 @@ def test_two_cells_per_thread_bitwise(lbm, orc, prec, prop, nx, halfway):
         fl[fl == 2] = 1
     f0 = random_state(orc, rng, dims, fl)
     outs = []
-    for cpt, threads in ((1, 64), (2, 32), (2, 64)):
+    for cpt, threads in ((1, 64), (2, 32), (2, 64), (2, 96)):
         h = lbm.lbm_create_lattice(lbm.make_desc(dims, prec, 0, prop), torch.cuda.current_stream())
         try:
             lbm.lbm_set_geometry(h, 0, fl)
@@ -367,4 +370,5 @@ def test_two_cells_per_thread_bitwise(lbm, orc, prec, prop, nx, halfway):
             outs.append(lbm.lbm_read_pdfs(h, 0))
         finally:
             lbm.lbm_destroy(h)
-    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    for k in range(1, len(outs)):
+        assert np.array_equal(outs[0], outs[k]), k
