@@ -15,6 +15,14 @@
 // per-node arithmetic, so the result is that of two one-step sweeps, bit for
 // bit. The region's one-cell rim and the first two planes of a segment are
 // computed twice (by neighbouring CTAs); their gathers mostly hit L2.
+//
+// The ring keeps each value only as long as step B needs it. Step B of plane z
+// pulls direction i from plane z - c_z(i) and, at a half-way wall, the
+// reflected direction from plane z itself; step A of plane p runs just before
+// step B of plane p - 1. So a value of plane p with c_z = +1 is last read by
+// step B of plane p + 1, and one with c_z = 0 or -1 by step B of plane p: the
+// three z-classes need 3, 2 and 2 plane slots, 43 direction planes in all
+// instead of 57, which lets more CTAs share an SM.
 #include <algorithm>
 #include <mutex>
 
@@ -25,6 +33,18 @@ namespace lbm {
 namespace {
 
 constexpr int kTbWidth = 32;   // region width in x
+
+// Ring layout by z-class: [c_z = -1: 5 directions x 2 slots][c_z = 0: 9 x 2][c_z = +1: 5 x 3].
+constexpr int kRingPlanes = 5 * 2 + 9 * 2 + 5 * 3;
+__host__ __device__ constexpr int ring_slots(int i) { return cz(i) > 0 ? 3 : 2; }
+__host__ __device__ constexpr int ring_rank(int i) {   // position of i among the directions of its z-class
+  int r = 0;
+  for (int k = 0; k < i; ++k) r += cz(k) == cz(i) ? 1 : 0;
+  return r;
+}
+__host__ __device__ constexpr int ring_first(int i) {   // first plane of direction i in the ring
+  return (cz(i) < 0 ? 0 : cz(i) == 0 ? 5 * 2 : 5 * 2 + 9 * 2) + ring_rank(i) * ring_slots(i);
+}
 
 __device__ __forceinline__ int wrap_mod(int a, int n) {
   const int r = a % n;
@@ -38,7 +58,7 @@ __global__ void __launch_bounds__(512) k_dense_pull_tb2(const S* __restrict__ sr
   ParamsT<S> pa, pb;
   begin_two_sweeps<S>(lp, pa, pb);
   extern __shared__ __align__(16) unsigned char tb_smem[];
-  S* ring = reinterpret_cast<S*>(tb_smem);   // [3 planes][19][TY][32]
+  S* ring = reinterpret_cast<S*>(tb_smem);   // [kRingPlanes][TY][32]
   const int TY = blockDim.y;
   const int rx = threadIdx.x, ry = threadIdx.y;
   const int plane = kTbWidth * TY;
@@ -47,9 +67,10 @@ __global__ void __launch_bounds__(512) k_dense_pull_tb2(const S* __restrict__ sr
   const int zs = blockIdx.z * seg, ze = min(zs + seg, nz);
   const bool interior = rx >= 1 && rx <= kTbWidth - 2 && ry >= 1 && ry <= TY - 2 && x0 + rx - 1 < nx &&
                         y0 + ry - 1 < ny;
-  auto slot = [](int z) { return (z + 3) % 3; };   // z >= -1
-  auto at = [&](int sl, int i, int dy, int dx) -> S* {
-    return ring + (size_t)(sl * Q + i) * plane + (ry + dy) * kTbWidth + (rx + dx);
+  // direction i of plane z (z >= -1) at offset (dx, dy) from this thread's cell
+  auto at = [&](int z, int i, int dy, int dx) -> S* {
+    const int sl = ring_first(i) + (z + 6) % ring_slots(i);
+    return ring + (size_t)sl * plane + (ry + dy) * kTbWidth + (rx + dx);
   };
 
   // step A on this thread's region cell of plane z (z in [-1, nz], wrapped)
@@ -64,9 +85,8 @@ __global__ void __launch_bounds__(512) k_dense_pull_tb2(const S* __restrict__ sr
       reverse(f);
     else
       Storage<S>::relax(f, pa, (uint32_t)n);
-    const int sl = slot(z);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) *at(sl, i, 0, 0) = Storage<S>::pack(f[i]);
+    for (int i = 0; i < Q; ++i) *at(z, i, 0, 0) = Storage<S>::pack(f[i]);
   };
 
   // step B on this thread's interior cell of plane z (z in [0, nz))
@@ -80,9 +100,9 @@ __global__ void __launch_bounds__(512) k_dense_pull_tb2(const S* __restrict__ sr
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if (kHW && i != 0 && flags[n + nb.up(i)] == kSolidHalfway)
-        f[i] = Storage<S>::unpack(*at(slot(z), opp(i), 0, 0));
+        f[i] = Storage<S>::unpack(*at(z, opp(i), 0, 0));
       else
-        f[i] = Storage<S>::unpack(*at(slot(z - cz(i)), i, -cy(i), -cx(i)));
+        f[i] = Storage<S>::unpack(*at(z - cz(i), i, -cy(i), -cx(i)));
     }
     if (fl == kSolidFullway)
       reverse(f);
@@ -96,7 +116,7 @@ __global__ void __launch_bounds__(512) k_dense_pull_tb2(const S* __restrict__ sr
   step_a(zs - 1);
   step_a(zs);
   for (int z = zs; z < ze; ++z) {
-    step_a(z + 1);   // overwrites the slot of plane z - 2, last read by step B of z - 1
+    step_a(z + 1);   // overwrites only slots whose last reader, step B of z - 1 or earlier, is done
     __syncthreads();
     step_b(z);
     __syncthreads();
@@ -105,7 +125,7 @@ __global__ void __launch_bounds__(512) k_dense_pull_tb2(const S* __restrict__ sr
 
 template <typename S>
 size_t tb_smem_bytes(int ty) {
-  return (size_t)3 * Q * kTbWidth * ty * sizeof(S);
+  return (size_t)kRingPlanes * kTbWidth * ty * sizeof(S);
 }
 
 // Largest TY (region rows) the shared memory allows for S, at most `want`.
@@ -137,8 +157,8 @@ cudaError_t tb_launch(const LatticeView& v, const S* src, S* dst, const ParamsT<
   const int segs = (int)std::max<int64_t>(1, std::min<int64_t>(want, v.nz / 8));
   const int seg = (v.nz + segs - 1) / segs;
   const dim3 grid((unsigned)tiles_x, (unsigned)tiles_y, (unsigned)((v.nz + seg - 1) / seg));
-  k_dense_pull_tb2<S, kHW><<<grid, dim3(kTbWidth, ty), smem, s>>>(src, dst, v.flags, v.nx, v.ny, v.nz, v.stride, seg,
-                                                                    p);
+  k_dense_pull_tb2<S, kHW><<<grid, dim3(kTbWidth, ty), smem, s>>>(src, dst, v.flags, v.nx, v.ny, v.nz,
+                                                                              v.stride, seg, p);
   return cudaGetLastError();
 }
 
