@@ -46,6 +46,36 @@ __host__ __device__ constexpr int ring_first(int i) {   // first plane of direct
   return (cz(i) < 0 ? 0 : cz(i) == 0 ? 5 * 2 : 5 * 2 + 9 * 2) + ring_rank(i) * ring_slots(i);
 }
 
+// Compile-time replay of a z segment's loop (step A of planes z0 - 1 and z0, then
+// for each z step A of z + 1 and step B of z) on tags of the values: every slot
+// index is in range and owned by one direction, and every value step B reads,
+// pulled or reflected, is the one step A wrote for that plane and direction.
+__host__ __device__ constexpr int ring_slot_of(int z, int i) { return ring_first(i) + (z + 6) % ring_slots(i); }
+constexpr bool ring_liveness_ok() {
+  int owner[kRingPlanes] = {};
+  for (int i = 0; i < Q; ++i)
+    for (int k = 0; k < ring_slots(i); ++k) {
+      const int sl = ring_first(i) + k;
+      if (sl < 0 || sl >= kRingPlanes || owner[sl] != 0) return false;
+      owner[sl] = i + 1;
+    }
+  for (int z0 = 0; z0 < 3; ++z0) {
+    int tag[kRingPlanes] = {};
+    auto tag_of = [](int z, int i) { return (z + 2) * 32 + i; };
+    for (int z = z0 - 1; z <= z0; ++z)
+      for (int i = 0; i < Q; ++i) tag[ring_slot_of(z, i)] = tag_of(z, i);
+    for (int z = z0; z < z0 + 12; ++z) {
+      for (int i = 0; i < Q; ++i) tag[ring_slot_of(z + 1, i)] = tag_of(z + 1, i);
+      for (int i = 0; i < Q; ++i) {
+        if (tag[ring_slot_of(z - cz(i), i)] != tag_of(z - cz(i), i)) return false;
+        if (tag[ring_slot_of(z, opp(i))] != tag_of(z, opp(i))) return false;
+      }
+    }
+  }
+  return true;
+}
+static_assert(ring_liveness_ok(), "a ring slot is overwritten before its last reader");
+
 __device__ __forceinline__ int wrap_mod(int a, int n) {
   const int r = a % n;
   return r < 0 ? r + n : r;
@@ -69,8 +99,7 @@ __global__ void __launch_bounds__(512) k_dense_pull_tb2(const S* __restrict__ sr
                         y0 + ry - 1 < ny;
   // direction i of plane z (z >= -1) at offset (dx, dy) from this thread's cell
   auto at = [&](int z, int i, int dy, int dx) -> S* {
-    const int sl = ring_first(i) + (z + 6) % ring_slots(i);
-    return ring + (size_t)sl * plane + (ry + dy) * kTbWidth + (rx + dx);
+    return ring + (size_t)ring_slot_of(z, i) * plane + (ry + dy) * kTbWidth + (rx + dx);
   };
 
   // step A on this thread's region cell of plane z (z in [-1, nz], wrapped)
