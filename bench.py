@@ -408,23 +408,13 @@ def microbench(lbm, stream, elem: int = 8, n: int = 1 << 24, reps: int = 5):
 
 def variant(lbm, stream, precision, propagation, steps, nf, peak, steps_per_pass=0):
     """The duct at another storage format or propagation, autotuned; with
-    steps_per_pass set, temporal blocking is fixed to it and the block size is
-    the fastest of 128, 256 and 512 threads over 8 timed steps."""
+    steps_per_pass set, temporal blocking is fixed to it after tuning (its
+    launch shape is fixed by the library)."""
     h, _ = make_duct(lbm, stream, precision, propagation)
     try:
         lbm.lbm_autotune(h, 4)
-        threads = None
         if steps_per_pass:
             lbm.lbm_set_temporal_blocking(h, steps_per_pass)
-            best = None
-            for t in (128, 256, 512):
-                lbm.lbm_set_tuning(h, t, 1)
-                lbm.lbm_step(h, 2)
-                dt = time_steps(lbm, h, 8, stream)
-                if best is None or dt < best[0]:
-                    best = (dt, t)
-            threads = best[1]
-            lbm.lbm_set_tuning(h, threads, 1)
         lbm.lbm_step(h, 4)
         sec = time_steps(lbm, h, steps, stream)
         spp = lbm.lbm_get_temporal_blocking(h)
@@ -435,11 +425,8 @@ def variant(lbm, stream, precision, propagation, steps, nf, peak, steps_per_pass
             lbm.LBM_F32_SHIFTED_DOUBLE_FLOAT: 4, lbm.LBM_F16_SHIFTED_STOCHASTIC: 2}[precision]
     bpf = bytes_per_flup(elem, False, "pull" if propagation == lbm.LBM_PULL_TWO_GRID else "aa") / spp
     gbs = mflups * 1e6 * bpf / 1e9
-    out = {"mflups": round(mflups, 1), "bytes_per_flup": bpf, "achieved_gbs": round(gbs, 1),
-           "roofline_frac": round(gbs / peak, 4), "steps": steps, "steps_per_pass": spp}
-    if threads:
-        out["threads"] = threads
-    return out
+    return {"mflups": round(mflups, 1), "bytes_per_flup": bpf, "achieved_gbs": round(gbs, 1),
+            "roofline_frac": round(gbs / peak, 4), "steps": steps, "steps_per_pass": spp}
 
 
 def run_sweep_only(args):

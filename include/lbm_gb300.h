@@ -186,12 +186,14 @@ int lbm_step(lbm_handle h, int32_t n);
 /* Temporal blocking of the two-grid pull sweep (listed by the paper among the
  * optimisations its kernels do not cover): with steps_per_pass = 2, runs of
  * steps of a single full-array pull lattice advance two steps per launch. A
- * CTA keeps the first step's post-collision values of three planes of a
- * 32 x TY tile in shared memory, rounded to the storage format as a stored
- * step would round them, and runs the second step one plane behind while it
- * marches along z, so each pass reads and writes the lattice once for two
- * steps. Results equal two one-step sweeps bit for bit. An odd remaining step
- * runs as a one-step sweep. lbm_autotune tries it for such lattices.
+ * CTA keeps the first step's post-collision values of a 32 x 8 region over
+ * the two or three planes the second step still needs in shared memory,
+ * rounded to the storage format as a stored step would round them, and runs
+ * the second step one plane behind while it marches along z, so each pass
+ * reads and writes the lattice once for two steps. Results equal two one-step
+ * sweeps bit for bit. The region is fixed (256 threads), so lbm_set_tuning's
+ * block size does not apply to these launches. An odd remaining step runs as
+ * a one-step sweep. lbm_autotune tries it for such lattices.
  * steps_per_pass = 1 (the default) turns it off. LBM_ERR_ARG unless 1 or 2;
  * LBM_ERR_UNSUPPORTED for 2 on batches, AA or indirect lattices. */
 int lbm_set_temporal_blocking(lbm_handle h, int32_t steps_per_pass);

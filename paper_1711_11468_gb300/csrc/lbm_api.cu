@@ -530,7 +530,7 @@ cudaError_t issue_step(lbm_handle h, int phase, cudaStream_t s) {
 // `phase` into the other one (the state then sits in buffer phase ^ 1).
 cudaError_t issue_two_steps(lbm_handle h, int phase, cudaStream_t s) {
   Lattice& L = h->lat[0];
-  return launch_sweep_pull2(sweep_view(h, 0), phase, L.pdf[phase], L.pdf[phase ^ 1], L.trt, h->threads, s);
+  return launch_sweep_pull2(sweep_view(h, 0), phase, L.pdf[phase], L.pdf[phase ^ 1], L.trt, s);
 }
 
 cudaError_t capture_graph(lbm_handle h, int phase, cudaGraphExec_t* exec) {
@@ -1049,8 +1049,8 @@ int lbm_autotune(lbm_handle h, int32_t steps) {
         for (int r : {1, 0})
           if ((c == 1 || dense) && (r == 1 || !dense))
             shapes.push_back({t, c, 0, dense ? h->run_indexing : r == 1, 1});
-    if (dense && h->prop == LBM_PULL_TWO_GRID)
-      for (int t : {128, 256, 512}) shapes.push_back({t, 1, 0, h->run_indexing, 2});
+    if (dense && h->prop == LBM_PULL_TWO_GRID)   // two steps per pass: one fixed launch shape
+      shapes.push_back({h->threads, h->cells_per_thread, 0, h->run_indexing, 2});
   }
   Shape best{h->threads, h->cells_per_thread, h->ctas_per_sm, h->run_indexing, h->steps_per_pass};
   float best_ms = 1e30f;

@@ -72,9 +72,9 @@ cudaError_t launch_sweep(const LatticeView& v, SweepKind kind, int parity, const
 
 // Two time steps of a full-array two-grid pull lattice in one launch (temporal
 // blocking, lbm_temporal.cu): src holds f(t), dst receives f(t+2). parity: the
-// sweep counter word to read (the handle's buffer index).
+// sweep counter word to read (the handle's buffer index). The launch shape is fixed.
 cudaError_t launch_sweep_pull2(const LatticeView& v, int parity, const void* src, void* dst, const TrtParams& p,
-                               int threads, cudaStream_t s);
+                               cudaStream_t s);
 
 // One time step of every lattice of a batch in one launch. d_lattices holds one
 // descriptor per lattice (batch_lattice_bytes(prec) bytes each, filled by

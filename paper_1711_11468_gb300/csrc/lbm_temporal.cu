@@ -4,12 +4,12 @@
 // values per cell, so one step per pass is bound by HBM at 2 x 19 x S bytes
 // per update; two steps per pass halve that.
 //
-// 2.5-D wavefront: a CTA owns an in-plane region of 32 x TY cells (one warp per
+// 2.5-D wavefront: a CTA owns an in-plane region of 32 x 8 cells (one warp per
 // region row) and marches along z over a segment of planes. For every plane z
 // it first runs step A (t -> t+1, gathering from the source grid in HBM) on the
 // whole region of plane z+1, keeping the post-collision values in a ring of
 // three planes in shared memory, then step B (t+1 -> t+2) on the interior
-// 30 x (TY-2) cells of plane z, gathering from the ring, and writes them to the
+// 30 x 6 cells of plane z, gathering from the ring, and writes them to the
 // destination grid. The ring values are rounded to the storage format exactly
 // as a one-step sweep stores them, and both steps use the one-step sweep's
 // per-node arithmetic, so the result is that of two one-step sweeps, bit for
@@ -33,6 +33,8 @@ namespace lbm {
 namespace {
 
 constexpr int kTbWidth = 32;   // region width in x
+constexpr int kTbRows = 8;     // region rows: one warp per row
+constexpr int kTbPlane = kTbWidth * kTbRows;
 
 // Ring layout by z-class: [c_z = -1: 5 directions x 2 slots][c_z = 0: 9 x 2][c_z = +1: 5 x 3].
 constexpr int kRingPlanes = 5 * 2 + 9 * 2 + 5 * 3;
@@ -82,24 +84,22 @@ __device__ __forceinline__ int wrap_mod(int a, int n) {
 }
 
 template <typename S, bool kHW>
-__global__ void __launch_bounds__(512) k_dense_pull_tb2(const S* __restrict__ src, S* __restrict__ dst,
+__global__ void __launch_bounds__(kTbPlane) k_dense_pull_tb2(const S* __restrict__ src, S* __restrict__ dst,
                                                         const uint8_t* __restrict__ flags, int nx, int ny, int nz,
                                                         int64_t stride, int seg, ParamsT<S> lp) {
   ParamsT<S> pa, pb;
   begin_two_sweeps<S>(lp, pa, pb);
   extern __shared__ __align__(16) unsigned char tb_smem[];
-  S* ring = reinterpret_cast<S*>(tb_smem);   // [kRingPlanes][TY][32]
-  const int TY = blockDim.y;
   const int rx = threadIdx.x, ry = threadIdx.y;
-  const int plane = kTbWidth * TY;
-  const int x0 = blockIdx.x * (kTbWidth - 2), y0 = blockIdx.y * (TY - 2);
+  S* const ring = reinterpret_cast<S*>(tb_smem) + ry * kTbWidth + rx;   // this thread's cell of ring plane 0
+  const int x0 = blockIdx.x * (kTbWidth - 2), y0 = blockIdx.y * (kTbRows - 2);
   const int gx = wrap_mod(x0 - 1 + rx, nx), gy = wrap_mod(y0 - 1 + ry, ny);
   const int zs = blockIdx.z * seg, ze = min(zs + seg, nz);
-  const bool interior = rx >= 1 && rx <= kTbWidth - 2 && ry >= 1 && ry <= TY - 2 && x0 + rx - 1 < nx &&
+  const bool interior = rx >= 1 && rx <= kTbWidth - 2 && ry >= 1 && ry <= kTbRows - 2 && x0 + rx - 1 < nx &&
                         y0 + ry - 1 < ny;
   // direction i of plane z (z >= -1) at offset (dx, dy) from this thread's cell
   auto at = [&](int z, int i, int dy, int dx) -> S* {
-    return ring + (size_t)ring_slot_of(z, i) * plane + (ry + dy) * kTbWidth + (rx + dx);
+    return ring + ring_slot_of(z, i) * kTbPlane + dy * kTbWidth + dx;
   };
 
   // step A on this thread's region cell of plane z (z in [-1, nz], wrapped)
@@ -153,65 +153,59 @@ __global__ void __launch_bounds__(512) k_dense_pull_tb2(const S* __restrict__ sr
 }
 
 template <typename S>
-size_t tb_smem_bytes(int ty) {
-  return (size_t)kRingPlanes * kTbWidth * ty * sizeof(S);
+constexpr size_t tb_smem_bytes() {
+  return (size_t)kRingPlanes * kTbPlane * sizeof(S);
 }
-
-// Largest TY (region rows) the shared memory allows for S, at most `want`.
-template <typename S>
-int tb_rows(int want) {
-  int ty = std::max(4, std::min(16, want));
-  while (ty > 4 && tb_smem_bytes<S>(ty) > (size_t)200 * 1024) ty /= 2;
-  return ty;
-}
+static_assert(tb_smem_bytes<double>() <= 200 * 1024, "ring of the 8-byte formats fits an SM");
 
 template <typename S, bool kHW>
-cudaError_t tb_launch(const LatticeView& v, const S* src, S* dst, const ParamsT<S>& p, int threads, cudaStream_t s) {
+cudaError_t tb_launch(const LatticeView& v, const S* src, S* dst, const ParamsT<S>& p, cudaStream_t s) {
   static std::once_flag once;
   std::call_once(once, [] {
     cudaFuncSetAttribute(k_dense_pull_tb2<S, kHW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)tb_smem_bytes<S>(tb_rows<S>(16)));
+                         (int)tb_smem_bytes<S>());
   });
-  const int ty = tb_rows<S>(threads / kTbWidth);
-  const size_t smem = tb_smem_bytes<S>(ty);
+  const size_t smem = tb_smem_bytes<S>();
   const int tiles_x = (v.nx + kTbWidth - 3) / (kTbWidth - 2);
-  const int tiles_y = (v.ny + ty - 3) / (ty - 2);
+  const int tiles_y = (v.ny + kTbRows - 3) / (kTbRows - 2);
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_pull_tb2<S, kHW>, kTbWidth * ty, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_pull_tb2<S, kHW>, kTbPlane, smem);
   // enough z segments for about four waves of resident CTAs, each at least 8 planes long
   const int64_t resident = (int64_t)std::max(1, sms) * std::max(1, per_sm);
   const int64_t want = (4 * resident + (int64_t)tiles_x * tiles_y - 1) / ((int64_t)tiles_x * tiles_y);
   const int segs = (int)std::max<int64_t>(1, std::min<int64_t>(want, v.nz / 8));
   const int seg = (v.nz + segs - 1) / segs;
   const dim3 grid((unsigned)tiles_x, (unsigned)tiles_y, (unsigned)((v.nz + seg - 1) / seg));
-  k_dense_pull_tb2<S, kHW><<<grid, dim3(kTbWidth, ty), smem, s>>>(src, dst, v.flags, v.nx, v.ny, v.nz,
-                                                                              v.stride, seg, p);
+  k_dense_pull_tb2<S, kHW><<<grid, dim3(kTbWidth, kTbRows), smem, s>>>(src, dst, v.flags, v.nx, v.ny, v.nz, v.stride,
+                                                                       seg, p);
   return cudaGetLastError();
 }
 
+// The region is fixed at 32 x 8 cells (256 threads), so the handle's block size does
+// not apply: ring addresses are then compile-time offsets from one base per thread.
 template <typename S>
-cudaError_t tb_typed(const LatticeView& v, int parity, const void* src, void* dst, const TrtParams& tp, int threads,
+cudaError_t tb_typed(const LatticeView& v, int parity, const void* src, void* dst, const TrtParams& tp,
                      cudaStream_t s) {
   const ParamsT<S> p = params_as<S>(tp, v, parity);
   if (v.has_halfway)
-    return tb_launch<S, true>(v, static_cast<const S*>(src), static_cast<S*>(dst), p, threads, s);
-  return tb_launch<S, false>(v, static_cast<const S*>(src), static_cast<S*>(dst), p, threads, s);
+    return tb_launch<S, true>(v, static_cast<const S*>(src), static_cast<S*>(dst), p, s);
+  return tb_launch<S, false>(v, static_cast<const S*>(src), static_cast<S*>(dst), p, s);
 }
 
 }  // namespace
 
 cudaError_t launch_sweep_pull2(const LatticeView& v, int parity, const void* src, void* dst, const TrtParams& p,
-                               int threads, cudaStream_t s) {
+                               cudaStream_t s) {
   if (v.indirect) return cudaErrorInvalidValue;
   switch (v.prec) {
-    case kF64: return tb_typed<double>(v, parity, src, dst, p, threads, s);
-    case kF32: return tb_typed<float>(v, parity, src, dst, p, threads, s);
-    case kF16: return tb_typed<__half>(v, parity, src, dst, p, threads, s);
-    case kF64DF: return tb_typed<f64df>(v, parity, src, dst, p, threads, s);
-    case kF32DF: return tb_typed<f32df>(v, parity, src, dst, p, threads, s);
-    case kF16SR: return tb_typed<h16sr>(v, parity, src, dst, p, threads, s);
+    case kF64: return tb_typed<double>(v, parity, src, dst, p, s);
+    case kF32: return tb_typed<float>(v, parity, src, dst, p, s);
+    case kF16: return tb_typed<__half>(v, parity, src, dst, p, s);
+    case kF64DF: return tb_typed<f64df>(v, parity, src, dst, p, s);
+    case kF32DF: return tb_typed<f32df>(v, parity, src, dst, p, s);
+    case kF16SR: return tb_typed<h16sr>(v, parity, src, dst, p, s);
   }
   return cudaErrorInvalidValue;
 }
