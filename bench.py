@@ -218,7 +218,7 @@ def porous_variant(lbm, stream, precision, propagation, steps, pack, peak):
         tuning = lbm.lbm_get_tuning(h)
     finally:
         lbm.lbm_destroy(h)
-    elem = {lbm.LBM_F64: 8, lbm.LBM_F32_SHIFTED: 4, lbm.LBM_F16_SHIFTED: 2,
+    elem = {lbm.LBM_F64: 8, lbm.LBM_F32_SHIFTED: 4, lbm.LBM_F16_SHIFTED: 2, lbm.LBM_F64_DOUBLE_FLOAT: 8,
             lbm.LBM_F16_SHIFTED_STOCHASTIC: 2}[precision]
     prop = "pull" if propagation == lbm.LBM_PULL_TWO_GRID else "aa"
     # index bytes per fluid update: pull reads the links every step, AA on odd steps only
@@ -564,6 +564,8 @@ def run_gpu(args):
                                                            peak)
         variants["f64_list_pull_porous256"] = porous_variant(lbm, stream, lbm.LBM_F64, lbm.LBM_PULL_TWO_GRID, vs,
                                                              pack, peak)
+        variants["f64_double_float_list_aa_porous256"] = porous_variant(lbm, stream, lbm.LBM_F64_DOUBLE_FLOAT,
+                                                                        lbm.LBM_AA_INPLACE, vs, pack, peak)
         variants["f32_list_aa_porous256"] = porous_variant(lbm, stream, lbm.LBM_F32_SHIFTED, lbm.LBM_AA_INPLACE, vs,
                                                            pack, peak)
         variants["f32_list_pull_porous256"] = porous_variant(lbm, stream, lbm.LBM_F32_SHIFTED, lbm.LBM_PULL_TWO_GRID,
