@@ -8,7 +8,7 @@
 // region row) and marches along z over a segment of planes. For every plane z
 // it first runs step A (t -> t+1, gathering from the source grid in HBM) on the
 // whole region of plane z+1, keeping the post-collision values in a ring of
-// three planes in shared memory, then step B (t+1 -> t+2) on the interior
+// planes in shared memory, then step B (t+1 -> t+2) on the interior
 // 30 x 6 cells of plane z, gathering from the ring, and writes them to the
 // destination grid. The ring values are rounded to the storage format exactly
 // as a one-step sweep stores them, and both steps use the one-step sweep's
@@ -22,7 +22,7 @@
 // step B of plane p - 1. So a value of plane p with c_z = +1 is last read by
 // step B of plane p + 1, and one with c_z = 0 or -1 by step B of plane p: the
 // three z-classes need 3, 2 and 2 plane slots, 43 direction planes in all
-// instead of 57, which lets more CTAs share an SM.
+// instead of the 57 of three whole planes, which lets more CTAs share an SM.
 #include <algorithm>
 #include <mutex>
 
