@@ -263,6 +263,7 @@ def batch_variant(lbm, stream, steps, peak):
         for k, sp in enumerate(specs):
             populate(h, k, sp, k)
         nf = sum(lbm.lbm_fluid_count(h, k) for k in range(len(specs)))
+        nf_list = sum(lbm.lbm_fluid_count(h, k) for k, sp in enumerate(specs) if sp.kind != "channel")
         ncells = sum(int(np.prod(sp.dims)) for sp in specs)
         lbm.lbm_autotune(h, 6)
         tuning = lbm.lbm_get_tuning(h)
@@ -294,8 +295,12 @@ def batch_variant(lbm, stream, steps, peak):
         for hh in singles:
             lbm.lbm_destroy(hh)
     n_list = sum(1 for sp in specs if sp.kind != "channel")
-    # bytes per fluid update: dense channels 152 (+ their solid walls), lists 152 + 36 (AA)
-    return {"mflups": round(mflups, 1), "lattices": len(specs), "fluid_cells": nf, "cells": ncells,
+    # bytes per fluid update: dense channels 152, lists 152 + 36 (AA: 72 B of links every other
+    # step), weighted by the fluid nodes of each kind
+    bpf = bytes_per_flup(4, False, "aa") + (bytes_per_flup(4, True, "aa") - bytes_per_flup(4, False, "aa")) * nf_list / nf
+    return {"mflups": round(mflups, 1), "lattices": len(specs), "fluid_cells": nf, "list_fluid_cells": nf_list,
+            "cells": ncells, "bytes_per_flup": round(bpf, 1),
+            "achieved_gbs": round(mflups * 1e6 * bpf / 1e9, 1), "roofline_frac": round(mflups * 1e6 * bpf / 1e9 / peak, 4),
             "porous_lattices": n_list, "tuning": {"threads": tuning[0], "cells_per_thread": tuning[1],
                                                   "ctas_per_sm": tuning[2]},
             "one_launch_per_lattice_mflups": round(single_mflups, 1), "steps": steps,
