@@ -611,6 +611,10 @@ def run_gpu(args):
             "roofline_hbm": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                              "frac": round(achieved / peak, 4), "bytes_per_flup": bpf,
                              "peak_source": peak_kind + " copy bandwidth"},
+            # per-cell view: all N cells counted as updated (solid walls included); the AA
+            # kernels skip solid cells, so their PDF bytes per cell update are bpf * N_f / N
+            "per_cell": {"cells": N, "mlups": round(value * N / nf, 1),
+                         "bytes_per_cell_update": round(bpf * nf / N, 1)},
             "microbench": micro,
             "tuning": {"threads": threads},
             "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
