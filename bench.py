@@ -395,8 +395,8 @@ def microbench(lbm, stream, elem: int = 8, n: int = 1 << 24, reps: int = 5):
             best = min(best, e0.elapsed_time(e1) / 1e3)
         out[name + "_gbs"] = round(2 * 19 * n * elem / best / 1e9, 1)
     del a, b
-    # FP64 pipe: 16 chains of FMAs per thread, 8 CTAs of 256 per SM
-    blocks, iters = torch.cuda.get_device_properties(0).multi_processor_count * 8, 2048
+    # FP64 pipe: 16 chains of FMAs per thread, one full wave of resident CTAs
+    blocks, iters = lbm.lbm_bench_fma64_wave(), 2048
     buf = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
     best = 1e30
     for _ in range(reps + 1):

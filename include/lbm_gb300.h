@@ -354,8 +354,11 @@ int lbm_bench_update19(void* buf, int64_t n, int64_t stride_elems, int32_t elem_
  * `iterations` FMAs and write their sums to out (device, blocks * 256 doubles,
  * caller-owned). Asynchronous on cuda_stream; the caller times it
  * (2 * 16 * iterations * blocks * 256 flops). LBM_ERR_ARG for NULL or
- * non-positive sizes. */
+ * non-positive sizes. lbm_bench_fma64_wave writes the number of such CTAs that
+ * the GPU holds at once (SMs x resident CTAs per SM), the block count that
+ * times the pipe without a partial second wave; LBM_ERR_ARG for NULL. */
 int lbm_bench_fma64(double* out, int32_t blocks, int32_t iterations, void* cuda_stream);
+int lbm_bench_fma64_wave(int32_t* blocks);
 
 #ifdef __cplusplus
 }

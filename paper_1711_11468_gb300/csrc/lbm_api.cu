@@ -1128,6 +1128,12 @@ int lbm_selftest_bounded_wait(lbm_handle h, int32_t polls) {
   return check_device_status(h);
 }
 
+int lbm_bench_fma64_wave(int32_t* blocks) {
+  if (!blocks) return fail(LBM_ERR_ARG, "null output");
+  *blocks = fma64_wave_blocks();
+  return LBM_OK;
+}
+
 int lbm_bench_fma64(double* out, int32_t blocks, int32_t iterations, void* cuda_stream) {
   if (!out || blocks < 1 || iterations < 1) return fail(LBM_ERR_ARG, "bad fma64 arguments");
   cudaError_t e = launch_fma64(out, blocks, iterations, static_cast<cudaStream_t>(cuda_stream));

@@ -86,6 +86,14 @@ cudaError_t launch_copy19(const void* src, void* dst, int64_t n, int64_t stride,
   return cudaGetLastError();
 }
 
+int fma64_wave_blocks() {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fma64, 256, 0);
+  return std::max(1, sms) * std::max(1, per_sm);
+}
+
 cudaError_t launch_fma64(double* out, int blocks, int iterations, cudaStream_t s) {
   k_fma64<<<blocks, 256, 0, s>>>(out, iterations);
   return cudaGetLastError();

@@ -157,6 +157,8 @@ cudaError_t launch_update19(void* buf, int64_t n, int64_t stride, int elem, cuda
 // FP64 fused multiply-add throughput: blocks x 256 threads, 16 x iterations FMAs
 // each; out[blocks * 256] receives the sums.
 cudaError_t launch_fma64(double* out, int blocks, int iterations, cudaStream_t s);
+// CTAs of the FMA probe that one wave of the whole GPU holds at once.
+int fma64_wave_blocks();
 // Bounded-wait self-test: sets the timeout bit of *status after `polls` polls.
 cudaError_t launch_wait_selftest(uint32_t polls, int* status, cudaStream_t s);
 

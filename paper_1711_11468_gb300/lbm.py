@@ -87,6 +87,7 @@ def load(path: str | None = None):
         "lbm_autotune_save": [ctypes.c_char_p],
         "lbm_autotune_load": [ctypes.c_char_p],
         "lbm_bench_fma64": [vp, i32, i32, vp],
+        "lbm_bench_fma64_wave": [ctypes.POINTER(i32)],
         "lbm_set_temporal_blocking": [H, i32],
         "lbm_get_temporal_blocking": [H, ctypes.POINTER(i32)],
         "lbm_get_run_indexing": [H, ctypes.POINTER(i32)],
@@ -398,6 +399,12 @@ def lbm_bench_copy19(src_ptr: int, dst_ptr: int, n: int, stride: int, elem_bytes
 
 def lbm_bench_fma64(out_ptr: int, blocks: int, iterations: int, stream=None):
     _check(load().lbm_bench_fma64(ctypes.c_void_p(out_ptr), int(blocks), int(iterations), _stream_ptr(stream)))
+
+
+def lbm_bench_fma64_wave() -> int:
+    out = ctypes.c_int32(0)
+    _check(load().lbm_bench_fma64_wave(ctypes.byref(out)))
+    return int(out.value)
 
 
 def lbm_bench_update19(buf_ptr: int, n: int, stride: int, elem_bytes: int, stream=None):

@@ -70,6 +70,8 @@ def test_argument_validation_without_gpu(lib):
     assert lib.lbm_read_pdfs(None, 0, None, 0) == lbm.LBM_ERR_ARG
     assert lib.lbm_set_allocator(lbm.ALLOC_FN(lambda n, c: 0), lbm.FREE_FN(), None) == lbm.LBM_ERR_ARG
     assert lib.lbm_bench_copy19(None, None, 10, 10, 8, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_bench_fma64(None, 1, 1, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_bench_fma64_wave(None) == lbm.LBM_ERR_ARG
     assert lib.lbm_set_stochastic_rounding(None, 1, 0) == lbm.LBM_ERR_ARG
     assert lib.lbm_set_run_indexing(None, 1) == lbm.LBM_ERR_ARG
     assert lib.lbm_set_temporal_blocking(None, 2) == lbm.LBM_ERR_ARG
