@@ -91,7 +91,8 @@ struct TrtSr : Trt<float> {
 // algebra, arranged so that each step is a fused multiply-add. The velocity
 // itself is never formed: rho u.u = |j|^2 / rho and (c.u)(c.j) = (c.j)^2 / rho,
 // so one reciprocal of rho scales the two quadratic terms (on the FP64 pipe,
-// which bounds the FP64 sweep, 131 -> 124 instructions per fluid cell, ncu).
+// which bounds the FP64 sweep, 131 -> 124 instructions per fluid cell, ncu; 121
+// with the Newton-refined reciprocal<double>).
 // With kShifted, f holds d_i = f_i - w_i: then rho = 1 + sum d_i, j = sum c_i d_i
 // (sum c_i w_i = 0), and e_i - w_i = w_i (drho - 3/2 rho u.u + 3 c.j + 9/2 (c.u)(c.j)),
 // the same pairwise algebra with rho replaced by drho in the constant term.
@@ -102,6 +103,28 @@ struct TrtSr : Trt<float> {
 // 3/2 of the u.u term and c4 divided by 2^14 and the force terms multiplied by
 // 2^14 (the constants in p carry the latter two). Powers of two scale exactly,
 // so this computes 2^14 times what the unscaled FP32 collision computes.
+// 1/rho for the collision. In FP64 the IEEE division costs 5 FP64 fused
+// multiply-adds on the pipe that bounds the FP64 sweep; here an FP32 reciprocal
+// of rho's leading 24 bits (relative error below 2^-22) is refined by one Newton
+// step in FP64, e = 1 - rho r0, r = r0 + r0 e, to a relative error of about 2^-44
+// in 2 FP64 instructions (the conversions are integer bit operations). 1/rho only
+// scales the quadratic terms of the equilibrium, (c.j)^2 / rho and |j|^2 / rho,
+// whose magnitude is below 1e-3 for |u| <= 0.03, so this error stays below 1e-16
+// absolute. Densities outside the normal FP32 range take the division.
+template <typename A>
+__device__ __forceinline__ A reciprocal(A rho) {
+  return A(1.0f) / rho;
+}
+template <>
+__device__ __forceinline__ double reciprocal<double>(double rho) {
+  bool out_of_range = false;
+  const float lead = split_f64_fast(rho, out_of_range).hi;
+  if (out_of_range) return 1.0 / rho;
+  const double r0 = f32_to_f64(__frcp_rn(lead));
+  const double e = fma(-rho, r0, 1.0);
+  return fma(r0, e, r0);
+}
+
 template <typename A, bool kShifted, bool kScaled = false>
 __device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
   A s[10], d[10];
@@ -116,7 +139,7 @@ __device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
   const A jx = (d[1] + d[4]) + (d[5] + d[6]) + d[7];
   const A jy = (d[2] + d[4]) - d[5] + (d[8] + d[9]);
   const A jz = (d[3] + d[6]) - d[7] + (d[8] - d[9]);
-  const A inv_rho = A(1.0f) / rho;
+  const A inv_rho = reciprocal<A>(rho);
   const A jsq = jx * jx + jy * jy + jz * jz;
   // constant part of e+ per unit weight: rho0 - 3/2 rho u.u = rho0 - 3/2 |j|^2 / rho
   const A base = rho0 - (A(kScaled ? 1.5f * kInvScale : 1.5f) * inv_rho) * jsq;
