@@ -350,7 +350,8 @@ __global__ void __launch_bounds__(512) k_list_aa_odd(S* __restrict__ pdf, const 
 // one elected thread has the next tile's 18 link rows already on their way
 // into the other shared-memory buffer by bulk copy. The gathers then depend on
 // a shared-memory read instead of a global load, and the 18 offsets need no
-// registers between the gather and the scatter.
+// registers between the gather and the scatter. The odd AA step works in place
+// on dst; its callers pass no src.
 constexpr int kStagedMaxThreads = 512;
 constexpr size_t staged_smem_bytes(int threads) { return (size_t)2 * 18 * threads * sizeof(uint32_t); }
 
@@ -658,10 +659,10 @@ cudaError_t sweep_typed(const LatticeView& v, SweepKind kind, int parity, const 
         if (ria)
           k_list_staged_ria<S, kAAOdd><<<staged_ria_grid<S, kAAOdd>(threads, ntiles), threads,
                                           staged_ria_smem_bytes(threads), s>>>(
-              dst, dst, v.ria_head, v.ria_pool, v.ria_chunk_start, v.n_nodes, v.stride, p, v.status);
+              nullptr, dst, v.ria_head, v.ria_pool, v.ria_chunk_start, v.n_nodes, v.stride, p, v.status);
         else if (v.status)
           k_list_staged<S, kAAOdd><<<staged_grid<S, kAAOdd>(threads, ntiles), threads, staged_smem_bytes(threads),
-                                      s>>>(dst, dst, v.link, v.n_nodes, v.stride, p, v.status);
+                                      s>>>(nullptr, dst, v.link, v.n_nodes, v.stride, p, v.status);
         else
           k_list_aa_odd<S><<<blocks, threads, 0, s>>>(dst, v.link, v.n_nodes, v.stride, p);
         break;
