@@ -33,11 +33,11 @@ from paper_1711_11468_gb300 import inputs  # noqa: E402
 WORKLOAD = inputs.DUCT_256
 DIMS = WORKLOAD["dims"]
 # FP64 pipe instructions per fluid lattice update of the FP64 AA sweep, from
-# ncu per-opcode counters of the current kernels (DADD 63, DFMA 42, DMUL 16 per
+# ncu per-opcode counters of the current kernels (DADD 63, DFMA 42, DMUL 14 per
 # fluid cell), the FP64 pipe's rate on GB300 (2 per clock per SM at 2.07 GHz),
 # and the DRAM bytes one launch of that sweep moves on the 256^3 duct
 # (dram__bytes_read + write of an even and an odd launch at full size, averaged).
-FP64_INSTR_PER_FLUP = 121.0
+FP64_INSTR_PER_FLUP = 119.0
 FP64_INSTR_PER_SEC = 152 * 2 * 2.07e9
 F64_AA_TRAFFIC_PER_LAUNCH = (2.529e9 + 2.449e9 + 2.703e9 + 2.489e9) / 2
 

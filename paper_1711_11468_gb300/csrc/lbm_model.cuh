@@ -10,6 +10,7 @@
 
 #include <cuda_fp16.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "lbm_df32.cuh"
 #include "lbm_sr.cuh"
@@ -92,7 +93,7 @@ struct TrtSr : Trt<float> {
 // itself is never formed: rho u.u = |j|^2 / rho and (c.u)(c.j) = (c.j)^2 / rho,
 // so one reciprocal of rho scales the two quadratic terms (on the FP64 pipe,
 // which bounds the FP64 sweep, 131 -> 124 instructions per fluid cell, ncu; 121
-// with the Newton-refined reciprocal<double>).
+// with the Newton-refined reciprocal<double>, 119 with half_exact).
 // With kShifted, f holds d_i = f_i - w_i: then rho = 1 + sum d_i, j = sum c_i d_i
 // (sum c_i w_i = 0), and e_i - w_i = w_i (drho - 3/2 rho u.u + 3 c.j + 9/2 (c.u)(c.j)),
 // the same pairwise algebra with rho replaced by drho in the constant term.
@@ -125,6 +126,20 @@ __device__ __forceinline__ double reciprocal<double>(double rho) {
   return fma(r0, e, r0);
 }
 
+// x / 2 without the FP64 pipe, by one less in the exponent field: exact for
+// normal x of magnitude at least 2^-1021, and x / 2 = x for zero, infinities and
+// NaN; only the lowest normal binade and subnormals (below 4.5e-308) would come
+// out wrong, and the collision never halves such values. No branch, so no FP64
+// instruction is issued. The edge constants are half the face constants
+// (w_edge = w_face / 2, so the host's w+ w_c and 9/2 w+ w_c are exactly halved
+// too), which lets the FP64 collision derive the two edge products from the face
+// products bit for bit.
+__device__ __forceinline__ double half_exact(double x) {
+  const int hi = __double2hiint(x);
+  const unsigned e = ((unsigned)hi >> 20) & 0x7FFu;
+  return __hiloint2double((e - 2u) < 0x7FDu ? hi - (1 << 20) : hi, __double2loint(x));
+}
+
 template <typename A, bool kShifted, bool kScaled = false>
 __device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
   A s[10], d[10];
@@ -143,8 +158,16 @@ __device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
   const A jsq = jx * jx + jy * jy + jz * jz;
   // constant part of e+ per unit weight: rho0 - 3/2 rho u.u = rho0 - 3/2 |j|^2 / rho
   const A base = rho0 - (A(kScaled ? 1.5f * kInvScale : 1.5f) * inv_rho) * jsq;
-  const A bw[2] = {p.wp_w[0] * base, p.wp_w[1] * base};   // w+ w_c base
-  const A c4r[2] = {p.c4[0] * inv_rho, p.c4[1] * inv_rho};   // 9/2 w+ w_c / rho
+  A bw[2], c4r[2];   // w+ w_c base and 9/2 w+ w_c / rho for the faces (c = 0) and the edges
+  bw[0] = p.wp_w[0] * base;
+  c4r[0] = p.c4[0] * inv_rho;
+  if constexpr (std::is_same<A, double>::value) {
+    bw[1] = half_exact(bw[0]);
+    c4r[1] = half_exact(c4r[0]);
+  } else {
+    bw[1] = p.wp_w[1] * base;
+    c4r[1] = p.c4[1] * inv_rho;
+  }
 
   f[0] = p.rest * f[0] + p.wp_w0 * base;
 

@@ -24,6 +24,8 @@ Trt<Arith<S>> trt_as(const TrtParams& p) {
     t.c4[c] = (A)(4.5 * p.omega_p * w[c]);
     t.c3[c] = (A)(3.0 * p.omega_m * w[c]);
   }
+  // w[1] = w[0] / 2 exactly, so the edge constants are exactly half the face
+  // constants; the FP64 collision relies on it (half_exact)
   for (int k = 0; k < 9; ++k) t.fk[k] = (A)p.fk[k];
   if (Storage<S>::kIncrement) {
     // return f*_i - f_i: the rest direction and the pair terms lose the f_i itself
