@@ -39,7 +39,7 @@ DIMS = WORKLOAD["dims"]
 # (dram__bytes_read + write of an even and an odd launch at full size, averaged).
 FP64_INSTR_PER_FLUP = 119.0
 FP64_INSTR_PER_SEC = 152 * 2 * 2.07e9
-F64_AA_TRAFFIC_PER_LAUNCH = (2.529e9 + 2.449e9 + 2.703e9 + 2.489e9) / 2
+F64_AA_TRAFFIC_PER_LAUNCH = (2.527e9 + 2.449e9 + 2.704e9 + 2.490e9) / 2
 
 METRIC = "MFLUP/s and % of HBM roofline, FP64 vs FP32/FP16-shifted vs batched, at stated error"
 UNIT = "MFLUP/s"
