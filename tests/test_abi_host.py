@@ -175,3 +175,45 @@ def test_pipe_and_blocks_geometry():
     b = inputs.blocks_flags(16, 16, 16, block=4, gap=4).reshape(16, 16, 16)
     assert b.sum() // 2 == 8 * 4 ** 3                          # 2 x 2 x 2 blocks of 4^3
     assert np.all(b[2:6, 2:6, 2:6] == 2) and np.all(b[0:2] == 0)
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "lbm_gb300.h"
+
+int main(void) {
+  lbm_handle h = 0;
+  lbm_desc d;
+  memset(&d, 0, sizeof d);
+  d.nx = 0; d.ny = 8; d.nz = 8;   /* a zero dimension: rejected before any CUDA call */
+  if (lbm_create_lattice(&d, NULL, &h) != LBM_ERR_ARG) return 1;
+  if (strlen(lbm_last_error()) == 0) return 2;
+  if (lbm_step(NULL, 1) != LBM_ERR_ARG) return 3;
+  if (lbm_destroy(NULL) != LBM_ERR_ARG) return 4;
+  puts(lbm_last_error());
+  return 0;
+}
+"""
+
+
+def test_header_compiles_as_c_and_the_library_links_from_c(lib, tmp_path):
+    """The boundary is a C ABI: a strict C11 program includes the header, links
+    against the library and calls it (argument checks only, no GPU needed)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    from paper_1711_11468_gb300 import lbm
+    libdir = os.path.dirname(lbm.LIB_PATH)
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "abi"
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.dirname(HEADER),
+                        str(src), "-L", libdir, "-llbm_gb300", f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert r.stdout.strip()
