@@ -79,31 +79,6 @@ struct TrtSr : Trt<float> {
   int parity;
 };
 
-// ---------------------------------------------------------------- collision
-// TRT collision plus body force on one node, in place on f[19].
-//   rho = sum f_i, j = sum c_i f_i, u = j / rho,
-//   e_i = w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u),
-//   per pair (k, k+9): f+ = (f_k + f_k+9)/2, f- = (f_k - f_k+9)/2 (same for e),
-//   f*_k = f_k - w+ (f+ - e+) - w- (f- - e-) + 3 w_k c_k.F, f*_k+9 mirrored.
-// Written per pair with s = f_k + f_k+9 and d = f_k - f_k+9 as
-//   P = (1 - w+) s/2 + w+ e+,  M = (1 - w-) d/2 + w- e- + 3 w_k c_k.F,
-//   f*_k = P + M,  f*_k+9 = P - M,
-// with e+ = w (rho - 3/2 rho u.u) + 9/2 w (c.u)(c.j) and e- = 3 w (c.j): the same
-// algebra, arranged so that each step is a fused multiply-add. The velocity
-// itself is never formed: rho u.u = |j|^2 / rho and (c.u)(c.j) = (c.j)^2 / rho,
-// so one reciprocal of rho scales the two quadratic terms (on the FP64 pipe,
-// which bounds the FP64 sweep, 131 -> 124 instructions per fluid cell, ncu; 121
-// with the Newton-refined reciprocal<double>, 119 with half_exact).
-// With kShifted, f holds d_i = f_i - w_i: then rho = 1 + sum d_i, j = sum c_i d_i
-// (sum c_i w_i = 0), and e_i - w_i = w_i (drho - 3/2 rho u.u + 3 c.j + 9/2 (c.u)(c.j)),
-// the same pairwise algebra with rho replaced by drho in the constant term.
-// With the increment constants (a - 1/2, b - 1/2, rest - 1) the same code
-// returns f*_i - f_i instead of f*_i.
-// With kScaled, f holds 2^14 d_i (the scaled stochastic FP16 format): the
-// collision of scaled values is the same code with rho = 1 + 2^-14 rho0, the
-// 3/2 of the u.u term and c4 divided by 2^14 and the force terms multiplied by
-// 2^14 (the constants in p carry the latter two). Powers of two scale exactly,
-// so this computes 2^14 times what the unscaled FP32 collision computes.
 // 1/rho for the collision. In FP64 the IEEE division costs 5 FP64 fused
 // multiply-adds on the pipe that bounds the FP64 sweep; here an FP32 reciprocal
 // of rho's leading 24 bits (relative error below 2^-22) is refined by one Newton
@@ -140,6 +115,31 @@ __device__ __forceinline__ double half_exact(double x) {
   return __hiloint2double((e - 2u) < 0x7FDu ? hi - (1 << 20) : hi, __double2loint(x));
 }
 
+// ---------------------------------------------------------------- collision
+// TRT collision plus body force on one node, in place on f[19].
+//   rho = sum f_i, j = sum c_i f_i, u = j / rho,
+//   e_i = w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u),
+//   per pair (k, k+9): f+ = (f_k + f_k+9)/2, f- = (f_k - f_k+9)/2 (same for e),
+//   f*_k = f_k - w+ (f+ - e+) - w- (f- - e-) + 3 w_k c_k.F, f*_k+9 mirrored.
+// Written per pair with s = f_k + f_k+9 and d = f_k - f_k+9 as
+//   P = (1 - w+) s/2 + w+ e+,  M = (1 - w-) d/2 + w- e- + 3 w_k c_k.F,
+//   f*_k = P + M,  f*_k+9 = P - M,
+// with e+ = w (rho - 3/2 rho u.u) + 9/2 w (c.u)(c.j) and e- = 3 w (c.j): the same
+// algebra, arranged so that each step is a fused multiply-add. The velocity
+// itself is never formed: rho u.u = |j|^2 / rho and (c.u)(c.j) = (c.j)^2 / rho,
+// so one reciprocal of rho scales the two quadratic terms (on the FP64 pipe,
+// which bounds the FP64 sweep, 131 -> 124 instructions per fluid cell, ncu; 121
+// with reciprocal<double> above, 119 with half_exact).
+// With kShifted, f holds d_i = f_i - w_i: then rho = 1 + sum d_i, j = sum c_i d_i
+// (sum c_i w_i = 0), and e_i - w_i = w_i (drho - 3/2 rho u.u + 3 c.j + 9/2 (c.u)(c.j)),
+// the same pairwise algebra with rho replaced by drho in the constant term.
+// With the increment constants (a - 1/2, b - 1/2, rest - 1) the same code
+// returns f*_i - f_i instead of f*_i.
+// With kScaled, f holds 2^14 d_i (the scaled stochastic FP16 format): the
+// collision of scaled values is the same code with rho = 1 + 2^-14 rho0, the
+// 3/2 of the u.u term and c4 divided by 2^14 and the force terms multiplied by
+// 2^14 (the constants in p carry the latter two). Powers of two scale exactly,
+// so this computes 2^14 times what the unscaled FP32 collision computes.
 template <typename A, bool kShifted, bool kScaled = false>
 __device__ __forceinline__ void collide(A (&f)[Q], const Trt<A>& p) {
   A s[10], d[10];
