@@ -342,7 +342,7 @@ const char* lbm_last_error(void);
 /* ----------------------------------------------------------------------
  * Bandwidth micro-benchmarks (Sec. 4.1): the GPU counterparts of the paper's
  * copy-19 (19 arrays copied concurrently) and update-19 (19 arrays updated in
- * place). Device pointers; arrays are `n` elements of `elem_bytes` (4 or 8)
+ * place). Device pointers; arrays are `n` elements of `elem_bytes` (2, 4 or 8)
  * each, at src + k*stride_elems (k = 0..18). Asynchronous on cuda_stream.
  * ---------------------------------------------------------------------- */
 int lbm_bench_copy19(const void* src, void* dst, int64_t n, int64_t stride_elems, int32_t elem_bytes,
