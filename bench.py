@@ -47,8 +47,14 @@ UNIT = "MFLUP/s"
 # Loop balance per fluid lattice update on a GPU (no write-allocate): 19 loads
 # and 19 stores of S bytes, plus the int32 adjacency for the fluid list
 # (18 entries every step for pull, every other step for AA).
-def bytes_per_flup(elem_bytes: int, indirect: bool, propagation: str) -> float:
+def bytes_per_flup(elem_bytes: int, indirect: bool, propagation: str, write_allocate: bool = False) -> float:
+    """Algorithmic bytes per fluid lattice update (the paper's loop balance, Table 1):
+    19 PDFs read and 19 written, plus on a CPU a write-allocate read of the stored
+    lines for one-step kernels with ordinary stores (a GPU has none), plus 18 4-byte
+    links for a list: every step for pull, every other step for AA."""
     b = 2 * 19 * elem_bytes
+    if write_allocate and propagation != "aa":
+        b += 19 * elem_bytes
     if indirect:
         b += 72 if propagation == "pull" else 36
     return float(b)
