@@ -342,9 +342,8 @@ def test_bounded_wait_timeout_is_reported(lbm):
 
 
 @pytest.mark.parametrize("halfway", [True, False])
-# odd: a lone last cell; even: the vector-access kernels, whose x-shifted
-# directions trade values between lanes (130 and 200: several warps per row,
-# the last one partly filled, and warp edges inside the row)
+# odd nx: a lone last cell and the per-cell fallback; even nx: the vector-access
+# pair kernels (130 and 200: several warps per row, the last one partly filled)
 @pytest.mark.parametrize("nx", [45, 46, 130, 200])
 @pytest.mark.parametrize("prec", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("prop", [0, 1])
