@@ -22,10 +22,11 @@ Parity status of each function (the pins live in ``tests/test_oracle_*.py``):
   macroscopic               pinned (analytic Poiseuille profile)
   splitmix64 / sr_bits      pinned (published splitmix64 outputs; an independent
                             numpy splitmix64; the documented bit layout)
-  round_half_stochastic     pinned (FP16 neighbours from numpy, the FP32 bit
-                            addition it restates, fixed points, exact mean over
-                            all 2^13 draws, odd symmetry, subnormal spacing,
-                            saturation)
+  round_half_stochastic     pinned (FP16 neighbours from numpy, monotone in the
+                            draw, the exact count of draws that round away from
+                            zero in every binade, subnormals included -- which
+                            together determine the rule -- fixed points, odd
+                            symmetry, subnormal spacing, saturation)
   step_f16_stochastic       pinned (every slot is an FP16 neighbour of the FP64
                             step's value; seed-averaged mass and momentum match
                             the FP64 step; full-way reversal is exact)

@@ -270,37 +270,30 @@ uint32_t orc_sr_bits(uint64_t seed, uint64_t t, uint64_t node, int j) {
   return (j % 2) == 0 ? (half & 0x1FFFu) : (half >> 19);
 }
 
-/* Stochastic rounding to FP16 (see the header). u and v are powers of two and
- * a / u is exact. In FP16's normal range r v / u = r / 2^13 and q + r / 2^13
- * is exact too; below it the sum is exact except for a in [2^-25, 2^-24),
- * where it may round in its last bit (q and r v / u span 54 bits there). */
+/* Stochastic rounding onto the FP16 grid (see the header). u is a power of
+ * two, so a / u, its floor and the remainder q are exact; the threshold
+ * 1 - r / 2^13 has 13 bits and is exact too, so the comparison decides
+ * exactly, in every binade. */
 double orc_round_half_stochastic(double x, uint32_t r, double* margin) {
   if (isnan(x) || isinf(x)) {
     if (margin) *margin = INFINITY;
     return x;
   }
   double a = fabs(x);
-  if (a == 0.0) {
-    if (margin) *margin = INFINITY;
-    return x;
-  }
   int e;
-  (void)frexp(a, &e);   /* a = m * 2^e, m in [0.5, 1): a in [2^(e-1), 2^e) */
-  int ex = e - 1;       /* a in [2^ex, 2^(ex+1)) */
-  int ve = ex < -126 ? -149 : ex - 23;
-  int ue = ex < -14 ? -24 : ex - 10;
+  (void)frexp(a, &e);                 /* a in [2^(e-1), 2^e) */
+  int ue = e - 1 >= -14 ? e - 11 : -24; /* FP16 spacing at a: 2^(ex-10) for a >= 2^-14 */
   double u = ldexp(1.0, ue);
-  double s = a / u;
-  double lo = floor(s);
-  double q = s - lo;
-  double up = q + (double)r * ldexp(1.0, ve - ue);
+  double lo = floor(a / u);
+  double q = a / u - lo;              /* remainder in spacings, in [0, 1) */
+  double thr = 1.0 - ldexp((double)r, -13);
   double res;
   if (q == 0.0) {
     res = lo * u;
     if (margin) *margin = INFINITY;
   } else {
-    res = (up >= 1.0 ? lo + 1.0 : lo) * u;
-    if (margin) *margin = fabs(up - 1.0);
+    res = (q >= thr ? lo + 1.0 : lo) * u;
+    if (margin) *margin = fabs(q - thr);
   }
   if (res > 65504.0) res = 65504.0;
   return x < 0 ? -res : res;

@@ -101,15 +101,15 @@ void orc_macroscopic(int nx, int ny, int nz, const uint8_t* flags, const double 
  * (m = 1..4). Direction j reads the 32-bit half (j mod 4) div 2 of
  * W_(j div 4) (0 = low) and takes its bits 0..12 for even j, 19..31 for odd j.
  *
- * Rounding rule (the addition of r to the magnitude bits of an FP32 number,
- * then truncation to FP16): with a = |x|, v = 2^(e-23) the FP32 spacing at a
- * (a in [2^e, 2^(e+1)); 2^-149 below 2^-126), u the FP16 spacing at a
- * (2^(e-10) for e >= -14, 2^-24 below), lo = u floor(a / u), the result is
- * sign(x) (lo + u) if a + r v >= lo + u, else sign(x) lo; finite results
- * saturate at 65504. For a in FP16's normal range, v = u / 2^13: an FP32 value
- * a rounds away from zero with probability exactly (a - lo) / u (unbiased).
- * Below 2^-14 the added amount is smaller than u, so there the rounding leans
- * towards zero (scaled, this is |d| < 2^-28).
+ * Rounding rule (stochastic rounding with a 13-bit draw): with a = |x|, u the
+ * FP16 spacing at a (2^(e-10) for a in [2^e, 2^(e+1)), e >= -14; 2^-24 below
+ * 2^-14, FP16's subnormal range), lo = u floor(a / u) and q = a / u - floor(a / u)
+ * the remainder in spacings, the result is sign(x) (lo + u) when
+ * q + r / 2^13 >= 1 and sign(x) lo otherwise; results beyond the FP16 range
+ * saturate at 65504. Over the 2^13 equally likely draws x rounds away from zero
+ * floor(2^13 q) times: the mean is x truncated to the grid of u / 2^13, which
+ * is x itself for an FP32 value in FP16's normal range (13 bits below u) and
+ * within u / 2^13 of x everywhere, subnormals included.
  * ------------------------------------------------------------------------ */
 
 /* log2 of the storage scale of the format: d * 2^14 is stored. */
@@ -122,9 +122,9 @@ uint64_t orc_splitmix64(uint64_t seed, uint64_t k);
 uint32_t orc_sr_bits(uint64_t seed, uint64_t t, uint64_t node, int j);
 
 /* Stochastic rounding of x to FP16 with random bits r (0..8191), the rule
- * above. If margin is not NULL it receives |(a + r v - lo - u) / u|, the
- * distance of the decision from its threshold in FP16 spacings (infinite when
- * x is an FP16 value). */
+ * above. If margin is not NULL it receives |q + r / 2^13 - 1|, the distance of
+ * the decision from its threshold in FP16 spacings (infinite when x is an FP16
+ * value or not finite). */
 double orc_round_half_stochastic(double x, uint32_t r, double* margin);
 
 /* The same over arrays: out[k] and margin[k] (margin may be NULL) for x[k], r[k]. */

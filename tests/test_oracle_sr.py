@@ -1,8 +1,10 @@
 """Pins of the oracle's scaled FP16 stochastic-rounding format: the
 counter-based generator against its published outputs and an independent
-implementation, the rounding rule against numpy's FP16 grid, against the FP32
-bit addition it restates and against its exact mean, and the step against the
-FP64 step it rounds. No GPU."""
+implementation; the rounding rule against numpy's FP16 grid (every result is a
+neighbour of x), against monotonicity in the draw and against the exact number
+of draws that round away from zero -- three properties that together fix the
+rule in every binade, FP16 subnormals included; and the step against the FP64
+step it rounds. No GPU."""
 import numpy as np
 import pytest
 
@@ -29,18 +31,6 @@ def scaled_neighbours(d):
 
 def random_magnitudes(rng, n, lo_exp=-30, hi_exp=15):
     return np.exp2(rng.uniform(lo_exp, hi_exp, n)) * rng.choice([-1.0, 1.0], n)
-
-
-def bit_add_then_truncate(x32, r):
-    """The mechanism the rule restates, written with numpy: add r to the bits
-    of the FP32 number, then truncate the result towards zero to FP16."""
-    y = (x32.view(np.uint32) + np.asarray(r, dtype=np.uint32)).view(np.float32).astype(np.float64)
-    with np.errstate(over="ignore"):
-        c = y.astype(np.float16)
-    c64 = c.astype(np.float64)
-    over = np.abs(c64) > np.abs(y)
-    c = np.where(over, np.nextafter(c, np.float16(0)), c)
-    return np.clip(c.astype(np.float64), -65504.0, 65504.0)
 
 
 # ------------------------------------------------------------- generator
@@ -92,35 +82,89 @@ def test_sr_bits_statistics(orc):
 
 
 # ---------------------------------------------------------- rounding rule
+def exact_ups(x):
+    """Number of the 2^13 draws that must round x away from zero for the mean
+    over all draws to be x truncated to the grid of u / 2^13, u the spacing of
+    numpy's FP16 grid at x: floor(2^13 (|x| - lo) / u), in exact rational
+    arithmetic."""
+    from fractions import Fraction
+    lo, hi = fp16_neighbours(np.array([x]))
+    a_lo, a_hi = sorted((abs(lo[0]), abs(hi[0])))
+    if a_hi == a_lo:
+        return 0, a_lo, a_hi
+    q = (Fraction(abs(float(x))) - Fraction(a_lo)) / (Fraction(a_hi) - Fraction(a_lo))
+    return int(q * 8192), a_lo, a_hi   # int() of a non-negative Fraction is its floor
+
+
 def test_round_half_gives_a_neighbour(orc):
     rng = np.random.default_rng(3)
-    x = random_magnitudes(rng, 20000)
+    x = random_magnitudes(rng, 20000, lo_exp=-45, hi_exp=15)
     r = rng.integers(0, 8192, x.size)
     got, margin = orc.round_half_stochastic(x, r)
     lo, hi = fp16_neighbours(x)
     inside = np.abs(x) < 65504
     assert np.all((got[inside] == lo[inside]) | (got[inside] == hi[inside]))
-    # the decision: away from zero iff |x| + r v reaches the neighbour away from zero,
-    # v the FP32 spacing at |x|
-    a = np.abs(x)
-    v = np.exp2(np.floor(np.log2(a)) - 23)
-    a_lo = np.minimum(np.abs(lo), np.abs(hi))
-    a_hi = np.maximum(np.abs(lo), np.abs(hi))
-    away = np.abs(got) == a_hi
-    sel = inside & (a_hi > a_lo)
-    assert np.array_equal(away[sel], (a + r * v >= a_hi)[sel])
-    assert np.allclose(margin[sel], (np.abs(a + r * v - a_hi) / (a_hi - a_lo))[sel], rtol=1e-9, atol=1e-12)
+    assert np.all(np.sign(got[got != 0]) == np.sign(x[got != 0]))
+    # the margin is the decision's distance from its threshold in spacings: never
+    # more than one spacing
+    assert np.all(margin[inside & np.isfinite(margin)] <= 1.0)
 
 
-def test_round_half_is_the_fp32_bit_addition(orc):
-    """For FP32 inputs the rule is: add r to the bit pattern, truncate to FP16."""
-    rng = np.random.default_rng(13)
-    x32 = random_magnitudes(rng, 50000, lo_exp=-40, hi_exp=16).astype(np.float32)
-    x32 = np.concatenate([x32, np.float32([0.0, -0.0, 65504.0, 65519.0, -65535.0, 2.0 ** -24, 2.0 ** -14])])
-    r = rng.integers(0, 8192, x32.size).astype(np.uint32)
-    got, _ = orc.round_half_stochastic(x32.astype(np.float64), r)
-    want = bit_add_then_truncate(x32, r)
-    assert np.array_equal(got, want)
+def binades():
+    """Magnitudes that span FP16's normal binades and its subnormal range, down
+    to below the smallest subnormal (2^-24), as FP64 and as FP32 values."""
+    rng = np.random.default_rng(5)
+    xs = list(random_magnitudes(rng, 16, lo_exp=-14, hi_exp=15))
+    xs += list(random_magnitudes(rng, 16, lo_exp=-24, hi_exp=-14))     # FP16 subnormals
+    xs += list(random_magnitudes(rng, 6, lo_exp=-38, hi_exp=-24))      # below 2^-24
+    xs += [1.0 / 3.0, 1e-4 + 1e-9, (600 + 0.75) * 2.0 ** -24, 0.75 * 2.0 ** -24, 2.0 ** -14 - 2.0 ** -40,
+           -(3 + 2.0 ** -12) * 2.0 ** -24, 2.0 ** -37, 2.0 ** -37 * 0.999]
+    xs += list(np.asarray(xs, dtype=np.float32).astype(np.float64))
+    return xs
+
+
+@pytest.mark.parametrize("x", binades())
+def test_round_half_over_all_draws(orc, x):
+    """Over all 2^13 draws: the result is monotone in the draw (a threshold
+    rule), and x rounds away from zero for exactly floor(2^13 q) draws, q the
+    remainder in spacings -- so the mean over the draws is x truncated to the
+    grid of u / 2^13 and x itself when x has no bits below that grid (every
+    FP32 value in FP16's normal range). Neighbours, monotonicity and this count
+    determine the rule completely; a rule that leans towards zero anywhere,
+    the subnormal range included, fails the count."""
+    from fractions import Fraction
+    r = np.arange(8192, dtype=np.uint32)
+    got, _ = orc.round_half_stochastic(np.full(r.size, x), r)
+    want_ups, a_lo, a_hi = exact_ups(x)
+    if a_hi == a_lo:   # an FP16 value: returned unchanged by every draw
+        assert np.all(got == x)
+        return
+    a = np.abs(got)
+    assert np.all((a == a_lo) | (a == a_hi))
+    away = a == a_hi
+    assert np.all(np.diff(away.astype(int)) >= 0)          # monotone: away for r >= r*
+    assert int(away.sum()) == want_ups
+    mean = sum(Fraction(float(v)) for v in got) / 8192
+    trunc = Fraction(a_lo) + Fraction(a_hi - a_lo) * Fraction(want_ups, 8192)
+    assert abs(mean) == trunc
+    assert 0 <= Fraction(abs(float(x))) - trunc < Fraction(a_hi - a_lo) / 8192
+    if float(np.float32(x)) == x and abs(x) >= 2.0 ** -14:
+        assert abs(mean) == Fraction(abs(float(x)))            # unbiased, exactly
+
+
+def test_round_half_subnormal_band_is_unbiased(orc):
+    """Below 2^-14 (FP16 subnormals, spacing 2^-24): a value 3/4 of the way to
+    the next grid point rounds up for 3/4 of the draws, as in every other
+    binade, and a value below the smallest subnormal rounds up to it with the
+    probability of its size in spacings."""
+    r = np.arange(8192, dtype=np.uint32)
+    for k, frac, ups in ((600, 0.75, 6144), (0, 0.75, 6144), (3, 0.5, 4096), (1023, 0.125, 1024),
+                         (0, 2.0 ** -13, 1), (0, 2.0 ** -13 * 0.999, 0)):
+        x0 = (k + frac) * 2.0 ** -24
+        got, _ = orc.round_half_stochastic(np.full(8192, x0), r)
+        assert (got > k * 2.0 ** -24).sum() == ups, (k, frac)
+        got, _ = orc.round_half_stochastic(np.full(8192, -x0), r)
+        assert (got < -k * 2.0 ** -24).sum() == ups, (k, frac)
 
 
 def test_round_half_fixed_points(orc):
@@ -133,26 +177,6 @@ def test_round_half_fixed_points(orc):
     assert np.all(np.isinf(margin))
 
 
-def test_round_half_mean_over_all_draws_is_x(orc):
-    """Over all 2^13 draws an FP32 value in FP16's normal range rounds away from
-    zero exactly (|x| - lo) / u of the time: the mean is x itself. A general
-    FP64 value is matched to within u / 2^13."""
-    rng = np.random.default_rng(5)
-    r = np.arange(8192, dtype=np.uint32)
-    for x in random_magnitudes(rng, 12, lo_exp=-14, hi_exp=15).astype(np.float32).astype(np.float64):
-        got, _ = orc.round_half_stochastic(np.full(r.size, x), r)
-        lo, hi = fp16_neighbours(np.array([x]))
-        u = hi[0] - lo[0]
-        if u == 0:
-            continue
-        ups = int(np.count_nonzero(got == hi[0]))
-        assert lo[0] + u * ups / 8192 == x
-    for x in list(random_magnitudes(rng, 12, lo_exp=-14, hi_exp=15)) + [1.0 / 3.0, 1e-4 + 1e-9]:
-        got, _ = orc.round_half_stochastic(np.full(r.size, x), r)
-        lo, hi = fp16_neighbours(np.array([x]))
-        assert abs(got.mean() - x) <= abs(hi[0] - lo[0]) / 8192 * (1 + 1e-12), x
-
-
 def test_round_half_odd_symmetry_and_subnormals(orc):
     rng = np.random.default_rng(9)
     x = random_magnitudes(rng, 5000, lo_exp=-40, hi_exp=-13)
@@ -163,11 +187,6 @@ def test_round_half_odd_symmetry_and_subnormals(orc):
     sub = np.abs(x) < 2.0 ** -14
     k = a[sub] / 2.0 ** -24   # FP16 subnormal range: whole multiples of 2^-24
     assert np.array_equal(k, np.round(k))
-    # below 2^-14 the added amount r 2^-38 covers half a spacing: a value 3/4 of the
-    # way to the next grid point rounds up for the draws r >= 2^12 only
-    x0 = (600 + 0.75) * 2.0 ** -24
-    got, _ = orc.round_half_stochastic(np.full(8192, x0), np.arange(8192, dtype=np.uint32))
-    assert (got > 600 * 2.0 ** -24).sum() == 4096
 
 
 def test_round_half_saturation_and_specials(orc):
