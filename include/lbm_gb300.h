@@ -135,7 +135,10 @@ typedef struct {
 
 /* Device allocator hook, process-wide, used by handles created afterwards.
  * alloc(bytes, ctx) returns a device pointer or NULL; free_(ptr, ctx).
- * Passing alloc == free_ == NULL restores cudaMalloc/cudaFree. */
+ * Passing alloc == free_ == NULL restores cudaMalloc/cudaFree. No counterpart
+ * in the paper (its closest concern is how the lattice and adjacency list are
+ * allocated, with huge pages, Sec. 2.2 "Huge Pages"); the hook lets the caller
+ * own device memory. LBM_ERR_ARG if exactly one of alloc and free_ is NULL. */
 typedef void* (*lbm_alloc_fn)(size_t bytes, void* ctx);
 typedef void (*lbm_free_fn)(void* ptr, void* ctx);
 int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_, void* ctx);
@@ -155,8 +158,14 @@ int lbm_create_batch(const lbm_desc* descs, int32_t count, void* cuda_stream, lb
 
 /* Set the geometry of lattice `lattice` from host flags uint8[N] (values 0, 1
  * or 2; 1 is rejected for indirect addressing, which stores fluid cells only).
- * Builds, on the device, the fluid list in lexicographic order and the
- * adjacency list (indirect), and allocates PDF storage. Synchronous. */
+ * Sec. 3 "Lattice Representation": the marker-and-cell full array with its
+ * flag field (direct addressing), or only the fluid nodes in a 1-D vector with
+ * an adjacency list (indirect addressing); the bounce-back kinds of the flags
+ * are those of Sec. 2 and Sec. 3.2. Builds, on the device, the fluid list in
+ * lexicographic order and the adjacency list (indirect), and allocates PDF
+ * storage. LBM_ERR_ARG for a flag value above 2, flag 1 on an indirect
+ * lattice, or an open non-periodic face; LBM_ERR_OOM if the allocator fails.
+ * Synchronous. */
 int lbm_set_geometry(lbm_handle h, int32_t lattice, const uint8_t* flags);
 
 /* Set the geometry to fluid everywhere except the cells inside the given
@@ -177,7 +186,11 @@ int lbm_set_params(lbm_handle h, int32_t lattice, double omega, double Lambda, c
 /* Initial state f_i(x, 0) = equilibrium(rho(x), u(x)) at fluid and full-way
  * solid cells; rho double[N] or NULL (1), u double[3][N] or NULL (0). The
  * equilibrium is the second-order w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u).
- * Resets the step counter to 0. Synchronous. */
+ * The paper does not write out its initial state; the verification set-up of
+ * Sec. 2.1 (a body-force-driven flow between two slabs) is read as starting
+ * from rest, rho = 1 and u = 0, which is what NULL pointers give. Resets the
+ * step counter to 0. LBM_ERR_STATE before set_geometry and set_params.
+ * Synchronous. */
 int lbm_init_equilibrium(lbm_handle h, int32_t lattice, const double* rho, const double* u);
 
 /* Advance every lattice of the handle by n >= 0 time steps (the fused
@@ -232,24 +245,38 @@ int lbm_adjacency_bytes(lbm_handle h, int32_t lattice, int64_t out[2]);
  * sweep < 0. Synchronous. */
 int lbm_set_stochastic_rounding(lbm_handle h, uint64_t seed, int64_t sweep);
 
-/* Wait for all work issued on the handle's stream. */
+/* Wait for all work issued on the handle's stream. No counterpart in the
+ * paper (its kernels run synchronously on the CPU). */
 int lbm_synchronize(lbm_handle h);
 
-/* Steps taken since the last init_equilibrium / write_pdfs. */
+/* Steps taken since the last init_equilibrium / write_pdfs (the iteration
+ * count of the benchmark loop, Sec. 2.1 "after enough iterations"). */
 int lbm_steps_done(lbm_handle h, int64_t* steps);
 
 /* Canonical PDFs f_i(x, t) of one lattice into out double[19*N] (out_len is
- * the element count, >= 19*N). Synchronous. */
+ * the element count, >= 19*N): the D3Q19 populations of Sec. 2 in the
+ * full-array order, after propagation and before collision. The AA pattern
+ * (Sec. 3 "AA Pattern Kernels") leaves them in swapped or shifted slots after
+ * an odd number of steps, and indirect lattices (Sec. 3 "Lattice
+ * Representation") store fluid nodes only; this call undoes both, un-shifts
+ * the reduced-precision formats and converts to FP64. LBM_ERR_ARG if out_len
+ * is too small; LBM_ERR_STATE before the state is initialised. Synchronous. */
 int lbm_read_pdfs(lbm_handle h, int32_t lattice, double* out, size_t out_len);
 
 /* Replace the state of one lattice by canonical PDFs in double[19*N]
- * (checkpoint restore; values at half-way solid cells are ignored). Resets
- * the step counter to 0. Synchronous. */
+ * (checkpoint restore; values at half-way solid cells are ignored), the
+ * inverse of lbm_read_pdfs: the same populations and layouts (Sec. 2, Sec. 3
+ * "Lattice Representation", "AA Pattern Kernels"), rounded to the storage
+ * format. Checkpointing itself has no counterpart in the paper. Resets the
+ * step counter to 0. LBM_ERR_ARG if in_len is too small. Synchronous. */
 int lbm_write_pdfs(lbm_handle h, int32_t lattice, const double* in, size_t in_len);
 
 /* Density rho double[N] and velocity u double[3][N] of one lattice, in FP64
  * from the canonical PDFs: rho = sum f_i, u = (sum c_i f_i + F/2) / rho;
- * 0 at solid cells. Either pointer may be NULL. Synchronous. */
+ * 0 at solid cells. The velocity field is what the verification set-up of
+ * Sec. 2.1 compares with the analytical Poiseuille solution; the F/2 term is
+ * the reading of the paper's constant body force taken here (a source added
+ * after collision). Either pointer may be NULL. Synchronous. */
 int lbm_read_macroscopic(lbm_handle h, int32_t lattice, double* rho, double* u);
 
 /* Mean of velocity component `comp` (0..2) over the fluid cells of every
@@ -260,7 +287,9 @@ int lbm_read_profile(lbm_handle h, int32_t lattice, int32_t axis, int32_t comp, 
 
 /* FP64 sums over every stored PDF of one lattice (fluid and full-way solid
  * cells): out[0] = sum_x sum_i f_i (mass), out[1..3] = sum_x sum_i c_i f_i
- * (momentum). Synchronous. */
+ * (momentum). Verification quantities for the set-up of Sec. 2.1: the TRT
+ * collision (Sec. 2) conserves mass and adds exactly the body force to the
+ * momentum of every fluid node. Synchronous. */
 int lbm_read_moments(lbm_handle h, int32_t lattice, double out[4]);
 
 /* The same sums as lbm_read_moments, computed by the same kernels, but this
@@ -280,10 +309,13 @@ int lbm_read_moments(lbm_handle h, int32_t lattice, double out[4]);
 int lbm_read_moments_noalloc(lbm_handle h, int32_t lattice, double out[4]);
 
 /* Flags uint8[N] of one lattice as the library holds them (for spheres: the
- * device voxelisation). Synchronous. */
+ * device voxelisation): the flag field of Sec. 3 "Lattice Representation".
+ * Synchronous. */
 int lbm_read_flags(lbm_handle h, int32_t lattice, uint8_t* out, size_t out_len);
 
-/* Number of fluid cells of one lattice. */
+/* Number of fluid cells of one lattice: the nodes a fluid lattice update
+ * (FLUP) counts in the paper's performance figures (Sec. 4.1, loop balance
+ * per fluid node update). LBM_ERR_STATE before set_geometry. */
 int lbm_fluid_count(lbm_handle h, int32_t lattice, int64_t* n_fluid);
 
 /* Adjacency list of an indirectly addressed lattice into out int32[18*Nf],
@@ -327,18 +359,25 @@ int lbm_autotune_save(const char* path);
 int lbm_autotune_load(const char* path);
 
 /* Device bytes the handle holds (flags, PDF storage, fluid and adjacency
- * lists, batch tables). */
+ * lists, batch tables). No counterpart in the paper. */
 int lbm_memory_bytes(lbm_handle h, int64_t* bytes);
 
+/* Free every device buffer of the handle (through the allocator it was
+ * created with) and the handle itself, after waiting for its stream.
+ * LBM_ERR_ARG for NULL.
+ * No counterpart in the paper. */
 int lbm_destroy(lbm_handle h);
 
-/* Exercise the bounded-wait path of the staged sweeps on purpose: one CTA arms
+/* No counterpart in the paper: a self-test of this library's failure path.
+ * Exercise the bounded-wait path of the staged sweeps on purpose: one CTA arms
  * an mbarrier for bytes that no copy delivers and gives up after `polls` polls
  * (1..2^20). Expected result: LBM_ERR_TIMEOUT, with the handle poisoned and the
  * CUDA context still usable. Nothing faults, traps or hangs. Synchronous. */
 int lbm_selftest_bounded_wait(lbm_handle h, int32_t polls);
 
-/* Thread-local message describing the last failed call ("" if none). */
+/* Thread-local message describing the last failed call ("" if none). No
+ * counterpart in the paper. The string stays valid until the calling thread's
+ * next call into the library. */
 const char* lbm_last_error(void);
 
 /* ----------------------------------------------------------------------
