@@ -1206,5 +1206,6 @@ extern "C" int lbm_read_moments_noalloc(lbm_handle h, int32_t lattice, double ou
   LBM_CUDA(h, launch_moments(v, current_layout(h), state, scratch, blocks, d_out, h->stream), "moments");
   LBM_CUDA(h, cudaMemcpyAsync(out, d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy moments");
   LBM_CUDA(h, cudaStreamSynchronize(h->stream), "moments sync");
-  return LBM_OK;
+  // Report a bounded wait that gave up in an earlier sweep, as lbm_read_moments does.
+  return check_device_status(h);
 }

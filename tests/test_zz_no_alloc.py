@@ -73,3 +73,28 @@ def test_noalloc_moments_match_allocating_call(lbm):
         for h in handles:
             lbm.lbm_destroy(h)
         lbm.lbm_set_allocator(None, None)
+
+
+def test_noalloc_reports_the_same_status(lbm):
+    """After a bounded wait has given up (the handle's device status word is
+    set and the handle poisoned), both calls refuse the handle with the same
+    status."""
+    import torch
+    h = lbm.lbm_create_lattice(lbm.make_desc((8, 8, 8), lbm.LBM_F64, lbm.LBM_DIRECT, lbm.LBM_AA_INPLACE),
+                               torch.cuda.current_stream())
+    try:
+        lbm.lbm_set_geometry(h, 0, np.zeros(512, dtype=np.uint8))
+        lbm.lbm_set_params(h, 0, 1.0, 3.0 / 16.0, (0.0, 0.0, 0.0))
+        lbm.lbm_init_equilibrium(h, 0)
+        assert np.array_equal(lbm.lbm_read_moments(h, 0), lbm.lbm_read_moments_noalloc(h, 0))
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_selftest_bounded_wait(h, 1000)
+        assert e.value.code == lbm.LBM_ERR_TIMEOUT
+        codes = []
+        for call in (lbm.lbm_read_moments, lbm.lbm_read_moments_noalloc):
+            with pytest.raises(lbm.LbmError) as e:
+                call(h, 0)
+            codes.append(e.value.code)
+        assert codes[0] == codes[1]
+    finally:
+        lbm.lbm_destroy(h)
