@@ -34,12 +34,15 @@ WORKLOAD = inputs.DUCT_256
 DIMS = WORKLOAD["dims"]
 # FP64 pipe instructions per fluid lattice update of the FP64 AA sweep, from
 # ncu per-opcode counters of the current kernels (DADD 63, DFMA 42, DMUL 14 per
-# fluid cell), the FP64 pipe's rate on GB300 (2 per clock per SM at 2.07 GHz),
-# and the DRAM bytes one launch of that sweep moves on the 256^3 duct
-# (dram__bytes_read + write of an even and an odd launch at full size, averaged).
+# fluid cell; profiles/dense_aa_f64_duct128_ncu.md, whose figure a CPU test keeps
+# equal to this one), the nominal FP64 pipe rate of GB300 (2 per clock per SM at
+# 2.07 GHz; the roofline's peak is the live probe's measured rate), and the DRAM
+# bytes one launch of that sweep moves on the 256^3 duct (dram__bytes_read +
+# write of an even and an odd launch at full size, averaged).
 FP64_INSTR_PER_FLUP = 119.0
-FP64_INSTR_PER_SEC = 152 * 2 * 2.07e9
+FP64_INSTR_PER_SEC_NOMINAL = 152 * 2 * 2.07e9
 F64_AA_TRAFFIC_PER_LAUNCH = (2.527e9 + 2.449e9 + 2.704e9 + 2.490e9) / 2
+GOLDEN_CHANNEL384 = os.path.join(ROOT, "tests", "golden", "channel384_oracle_profile.txt")
 
 METRIC = "MFLUP/s and % of HBM roofline, FP64 vs FP32/FP16-shifted vs batched, at stated error"
 UNIT = "MFLUP/s"
@@ -171,10 +174,10 @@ def sum_over_ranks(x: float, world: int, device=None) -> float:
 
 
 # ----------------------------------------------------------------- GPU arm
-def make_duct(lbm, stream, precision, propagation, host_u=None):
+def make_duct(lbm, stream, precision, propagation, host_u=None, host_flags=None):
     desc = lbm.make_desc(DIMS, precision, lbm.LBM_DIRECT, propagation, periodic=(1, 0, 0))
     h = lbm.lbm_create_lattice(desc, stream)
-    flags = inputs.duct_flags(*DIMS)
+    flags = inputs.duct_flags(*DIMS) if host_flags is None else host_flags
     lbm.lbm_set_geometry(h, 0, flags)
     lbm.lbm_set_params(h, 0, WORKLOAD["omega"], WORKLOAD["Lambda"], WORKLOAD["force"])
     if host_u is None:
@@ -401,19 +404,80 @@ def microbench(lbm, stream, elem: int = 8, n: int = 1 << 24, reps: int = 5):
             best = min(best, e0.elapsed_time(e1) / 1e3)
         out[name + "_gbs"] = round(2 * 19 * n * elem / best / 1e9, 1)
     del a, b
-    # FP64 pipe: 16 chains of FMAs per thread, one full wave of resident CTAs
-    blocks, iters = lbm.lbm_bench_fma64_wave(), 2048
+    return out
+
+
+def fp64_pipe_rate(lbm, stream, iterations: int = 8192, reps: int = 5) -> float:
+    """FP64 pipe throughput in G FP64 instructions per second: one full wave of
+    resident CTAs, each thread running 16 independent chains of fused
+    multiply-adds (about 60 ms per launch); one untimed launch first, then the
+    best of `reps`. Chain counts of 4 to 32, blocks of 128 to 1024 threads and
+    add or multiply chains all read the same rate on GB300."""
+    import torch
+    blocks = lbm.lbm_bench_fma64_wave()
     buf = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
     best = 1e30
-    for _ in range(reps + 1):
+    for r in range(reps + 1):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        lbm.lbm_bench_fma64(buf.data_ptr(), blocks, iters, stream)
+        lbm.lbm_bench_fma64(buf.data_ptr(), blocks, iterations, stream)
         e1.record(stream)
         e1.synchronize()
-        best = min(best, e0.elapsed_time(e1) / 1e3)
-    out["fp64_fma_per_s_g"] = round(16 * iters * blocks * 256 / best / 1e9, 1)
+        if r > 0:
+            best = min(best, e0.elapsed_time(e1) / 1e3)
     del buf
+    return 16.0 * iterations * blocks * 256 / best / 1e9
+
+
+def read_golden_profile(path=GOLDEN_CHANNEL384):
+    vals = {}
+    with open(path) as fh:
+        for ln in fh:
+            if ln.startswith("#") or not ln.strip():
+                continue
+            y, v = ln.split()
+            vals[int(y)] = float.fromhex(v)
+    return np.array([vals[y] for y in range(len(vals))])
+
+
+def accuracy_channel384(lbm, stream):
+    """Every storage format on the 384^3 body-force channel (F = 1e-7, 5000 AA
+    steps from rest, the Sec. 2.1 verification set-up at the reduced-precision
+    workload's size): the mean velocity profile u_x(y) against the FP64
+    oracle's profile (stored by tests/golden/make_channel384_profile.py; the
+    oracle is not run here) and against the start-up series at t + 1/2."""
+    c = inputs.CHANNEL_384
+    dims, steps = c["dims"], c["steps"]
+    ny = dims[1]
+    ref = read_golden_profile()
+    nu = (1.0 / c["omega"] - 0.5) / 3.0
+    ana = startup_series(np.arange(ny, dtype=float), steps + 0.5, c["force"][0], nu, 0.5, ny - 1.5)
+    m = slice(1, ny - 1)
+    out = {"workload": "channel 384^3, F = 1e-7 along x, omega 1, Lambda 3/16, 5000 AA steps from rest",
+           "oracle_max_rel_vs_analytic": float(np.abs(ref[m] - ana[m]).max() / np.abs(ana[m]).max()),
+           "target_f32": 1e-5}
+    names = [("f64", lbm.LBM_F64), ("f64_double_float", lbm.LBM_F64_DOUBLE_FLOAT),
+             ("f32_shifted", lbm.LBM_F32_SHIFTED), ("f32_shifted_double_float", lbm.LBM_F32_SHIFTED_DOUBLE_FLOAT),
+             ("f16_shifted", lbm.LBM_F16_SHIFTED), ("f16_shifted_stochastic", lbm.LBM_F16_SHIFTED_STOCHASTIC)]
+    ncells = float(np.prod(dims))
+    for name, prec in names:
+        h = lbm.lbm_create_lattice(lbm.make_desc(dims, prec, lbm.LBM_DIRECT, lbm.LBM_AA_INPLACE, (1, 0, 1)), stream)
+        try:
+            lbm.lbm_set_geometry(h, 0, inputs.channel_flags(*dims))
+            lbm.lbm_set_params(h, 0, c["omega"], c["Lambda"], c["force"])
+            lbm.lbm_init_equilibrium(h, 0)
+            lbm.lbm_step(h, steps)
+            prof = lbm.lbm_read_profile(h, 0, 1, 0)
+            mass = lbm.lbm_read_moments(h, 0)[0]
+        finally:
+            lbm.lbm_destroy(h)
+        out[name] = {
+            "max_rel_vs_oracle": float(np.abs(prof[m] - ref[m]).max() / np.abs(ref[m]).max()),
+            "l2_rel_vs_oracle": float(np.linalg.norm(prof[m] - ref[m]) / np.linalg.norm(ref[m])),
+            "max_rel_vs_analytic": float(np.abs(prof[m] - ana[m]).max() / np.abs(ana[m]).max()),
+            "l2_rel_vs_analytic": float(np.linalg.norm(prof[m] - ana[m]) / np.linalg.norm(ana[m])),
+            "mass_rel_drift": float(abs(mass - ncells) / ncells),
+        }
     return out
 
 
@@ -532,26 +596,38 @@ def run_gpu(args):
     bpf = bytes_per_flup(8, False, "aa")
     achieved = value / world * 1e6 * bpf / 1e9
 
-    # end to end through the C ABI from host buffers: geometry + initial field
-    # up, K steps, density and velocity back
-    host_u = inputs.velocity_perturbation(*DIMS, seed=WORKLOAD["seed"], amplitude=WORKLOAD["amplitude"],
-                                          flags=flags)
+    # the FP64 pipe's measured rate, the denominator of the sweep's ALU roofline
+    fp64_rate_g = fp64_pipe_rate(lbm, stream)
+
+    # end to end through the C ABI from pinned host buffers: the geometry and the
+    # initial velocity field up, K steps, density and velocity back. The host
+    # buffers are allocated and filled before the timed region; the launch shape
+    # comes from the autotuner's cache (the signature was tuned above).
     N = flags.size
-    rho_out, u_out = np.empty(N), np.empty((3, N))
+    pinned = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+    flags_in = pinned((N,), torch.uint8)
+    flags_in[:] = flags
+    u_in = pinned((3, N), torch.float64)
+    u_in[:] = inputs.velocity_perturbation(*DIMS, seed=WORKLOAD["seed"], amplitude=WORKLOAD["amplitude"],
+                                           flags=flags)
+    rho_out, u_out = pinned((N,), torch.float64), pinned((3, N), torch.float64)
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h2, _ = make_duct(lbm, stream, lbm.LBM_F64, lbm.LBM_AA_INPLACE, host_u=host_u)
+    h2, _ = make_duct(lbm, stream, lbm.LBM_F64, lbm.LBM_AA_INPLACE, host_u=u_in, host_flags=flags_in)
+    lbm.lbm_autotune(h2, 4)
     lbm.lbm_step(h2, args.steps)
     lbm.lbm_read_macroscopic(h2, 0, rho_out, u_out)
     e2e_sec = time.perf_counter() - t0
     lbm.lbm_destroy(h2)
     e2e_sec = max_over_ranks(e2e_sec, world, f"cuda:{local}")
     e2e_value = whole_job_mflups(nf * args.steps, world, e2e_sec)
+    del flags_in, u_in, rho_out, u_out
 
     variants = {}
     micro = {}
     accuracy = {}
+    accuracy384 = {}
     if rank == 0 and not args.no_variants:
         vs = min(args.steps, 200)
         variants["f64_pull_two_grid"] = variant(lbm, stream, lbm.LBM_F64, lbm.LBM_PULL_TWO_GRID, vs, nf, peak)
@@ -587,20 +663,23 @@ def run_gpu(args):
         variants["f32_aa_geometries256"] = geometry_sweep(lbm, stream, min(args.steps, 50))
         micro = microbench(lbm, stream)
         accuracy = accuracy_poiseuille64(lbm, stream)
+        accuracy384 = accuracy_channel384(lbm, stream)
 
-    # The FP64 sweep is bound by the FP64 pipe (2 FMA per clock per SM on GB300):
-    # its ALU roofline counts FP64 pipe instructions per fluid update (ncu).
-    fp64_rate = FP64_INSTR_PER_SEC
-    alu_achieved = value / world * 1e6 * FP64_INSTR_PER_FLUP
-    alu = {"bound": "alu", "achieved": round(alu_achieved / 1e9, 1), "peak": round(fp64_rate / 1e9, 1),
-           "unit": "G FP64 instr/s", "frac": round(alu_achieved / fp64_rate, 4),
+    # The FP64 sweep is bound by the FP64 pipe: its ALU roofline counts FP64 pipe
+    # instructions per fluid update (ncu) against the pipe's measured rate.
+    alu_achieved = value / world * 1e6 * FP64_INSTR_PER_FLUP / 1e9
+    alu = {"bound": "alu", "achieved": round(alu_achieved, 1), "peak": round(fp64_rate_g, 1),
+           "unit": "G FP64 instr/s", "frac": round(alu_achieved / fp64_rate_g, 4),
            "traffic": F64_AA_TRAFFIC_PER_LAUNCH,
            "traffic_per_fluid_cell": (round(F64_AA_TRAFFIC_PER_LAUNCH / nf, 1) if F64_AA_TRAFFIC_PER_LAUNCH else None),
            "instr_per_flup": FP64_INSTR_PER_FLUP,
-           "peak_source": "152 SMs x 2 FP64 FMA/clock x 2.07 GHz (nominal; live probe: microbench fp64_fma_per_s_g)"}
-    roofline = alu if alu["frac"] > achieved / peak else {
-        "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-        "frac": round(achieved / peak, 4), "traffic": None, "bytes_per_flup": bpf, "peak_source": peak_kind}
+           "peak_source": "measured: live FP64 FMA probe (one wave of resident CTAs, 16 chains per thread)",
+           "peak_nominal": round(FP64_INSTR_PER_SEC_NOMINAL / 1e9, 1),
+           "frac_of_nominal": round(alu_achieved * 1e9 / FP64_INSTR_PER_SEC_NOMINAL, 4)}
+    hbm = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+           "frac": round(achieved / peak, 4), "bytes_per_flup": bpf, "target_frac": 0.8,
+           "peak_source": peak_kind + " copy bandwidth"}
+    roofline = alu if alu["frac"] > hbm["frac"] else dict(hbm, traffic=None)
 
     if rank == 0:
         line = {
@@ -614,14 +693,12 @@ def run_gpu(args):
                        "Lambda": WORKLOAD["Lambda"], "l2": "inputs larger than L2 (2.55 GB lattice)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
-            "roofline_hbm": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                             "frac": round(achieved / peak, 4), "bytes_per_flup": bpf,
-                             "peak_source": peak_kind + " copy bandwidth"},
+            "roofline_hbm": hbm,
             # per-cell view: all N cells counted as updated (solid walls included); the AA
             # kernels skip solid cells, so their PDF bytes per cell update are bpf * N_f / N
             "per_cell": {"cells": N, "mlups": round(value * N / nf, 1),
                          "bytes_per_cell_update": round(bpf * nf / N, 1)},
-            "microbench": micro,
+            "microbench": dict(micro, fp64_fma_per_s_g=round(fp64_rate_g, 1)),
             "tuning": {"threads": threads},
             "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
                     "h2d_bytes_per_step": (N + 3 * N * 8) / args.steps,
@@ -631,6 +708,7 @@ def run_gpu(args):
             "mass_after": moments[0],
             "variants": variants,
             "accuracy_poiseuille64_max_rel": accuracy,
+            "accuracy_channel384": accuracy384,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

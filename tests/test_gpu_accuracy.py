@@ -17,19 +17,24 @@ from paper_1711_11468_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-# Max-relative error bound of the profile against the FP64 oracle, per storage
-# format. FP64 arithmetic and the double-float collision both sit near 1e-10
-# after 5000 steps: the profile (u ~ 5e-4) is a cancelling sum of PDFs of size
-# ~0.1 whose round-off walks randomly, about 1e-13 in u, on either side. FP32
-# storage misses the 1e-5 target (about 4e-5: the 1e-8-per-step force increment
-# is rounded against values near 1e-4); FP16 storage stagnates (the increments
-# fall below its resolution), so its bound only asks for a finite result.
-# FP32 storage with the double-float collision meets the 1e-5 target: the
-# stored values are rounded once per step, without the correlated rounding of
-# FP32 arithmetic. FP16 storage with stochastic rounding keeps the increments
-# on average; what is left is the noise of the random rounding, averaged over
-# the 384^2 cells of a plane: 4.2e-5, as close as FP32 storage gets.
-BOUNDS = {0: 1e-9, 3: 1e-9, 1: 1e-4, 2: 1.5, 4: 1e-5, 5: 1e-4}
+# Max-relative error of the profile against the FP64 oracle, per storage format:
+# (lower, upper) bounds around the values measured on GB300, with the verdict each
+# records against the workload's FP32 target of 1e-5.
+#  - FP64 and FP64 storage with the double-float collision: about 1e-10, the random
+#    round-off walk of a profile (u ~ 5e-4) built from PDFs of size ~0.1.
+#  - FP32 storage MISSES the target (measured 4.2e-5): the 1e-8-per-step force
+#    increment is rounded against values near 1e-4, with FP32 collision arithmetic.
+#  - FP32 storage with the double-float collision MEETS it (measured 3.3e-6): the
+#    stored values are rounded once per step, without the correlated rounding of
+#    FP32 arithmetic.
+#  - FP16 storage STAGNATES (measured 1.0): the increments fall below half an FP16
+#    spacing, so the profile stays at rest; the lower bound asserts the stagnation.
+#  - Scaled FP16 storage with stochastic rounding keeps the increments on average
+#    (measured 4.4e-5): the noise of the random rounding averaged over the 384^2
+#    cells of a plane, the level of FP32 storage, at half its bytes.
+BOUNDS = {0: (0.0, 1e-9), 3: (0.0, 1e-9), 1: (1e-5, 8e-5), 4: (0.0, 1e-5), 2: (0.9, 1.1), 5: (0.0, 8e-5)}
+VERDICT = {0: "round-off", 3: "round-off", 1: "misses 1e-5", 4: "meets 1e-5", 2: "stagnates",
+           5: "FP32 level"}
 
 
 def series(y, t, F, nu, a, b, nterms=4001):
@@ -95,4 +100,5 @@ def test_channel384_profile_error(lbm, reference, prec):
             json.dump({"workload": "channel 384^3, F=1e-7, omega=1, Lambda=3/16, 5000 steps, AA",
                        "errors": REPORT}, fh, indent=1)
     assert np.all(np.isfinite(prof))
-    assert err["max_rel_vs_oracle"] <= BOUNDS[prec], err
+    lo, hi = BOUNDS[prec]
+    assert lo <= err["max_rel_vs_oracle"] <= hi, (VERDICT[prec], err)

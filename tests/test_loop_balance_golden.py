@@ -70,3 +70,54 @@ def test_run_indexed_links_within_the_papers_ria_band(orc):
     bl = 304.0 + 0.5 * run_indexed_bytes_per_node(link, nf)
     assert 304.0 < bl <= 342.0
     assert bl < 310.0, bl
+
+
+def read_channel384_profile():
+    path = os.path.join(os.path.dirname(__file__), "golden", "channel384_oracle_profile.txt")
+    vals = {}
+    with open(path) as fh:
+        for ln in fh:
+            if ln.startswith("#") or not ln.strip():
+                continue
+            y, v = ln.split()
+            vals[int(y)] = float.fromhex(v)
+    return np.array([vals[y] for y in range(len(vals))])
+
+
+def test_channel384_golden_profile_is_the_oracle_and_the_series(orc):
+    """The stored 384^3 channel profile (read by the benchmark's accuracy
+    table) is what the oracle computes now, bit for bit, and it follows the
+    analytic start-up series of plane Poiseuille flow at t + 1/2 (Sec. 2.1
+    verification set-up) to 5e-5 max-relative."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "make_channel384_profile", os.path.join(os.path.dirname(__file__), "golden", "make_channel384_profile.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    stored = read_channel384_profile()
+    assert np.array_equal(stored, mod.compute())
+    ny = 384
+    nu = (1.0 / 1.0 - 0.5) / 3.0
+    y = np.arange(ny, dtype=float)
+    a, b = 0.5, ny - 1.5
+    L = b - a
+    ana = 1e-7 / (2 * nu) * (y - a) * (b - y)
+    for n in range(1, 4001, 2):
+        ana -= 4 * 1e-7 * L * L / (nu * np.pi ** 3 * n ** 3) * np.sin(n * np.pi * (y - a) / L) \
+            * np.exp(-nu * n * n * np.pi ** 2 * 5000.5 / L ** 2)
+    m = slice(1, ny - 1)
+    assert np.abs(stored[m] - ana[m]).max() / np.abs(ana[m]).max() < 5e-5
+    assert stored[0] == 0 and stored[ny - 1] == 0
+
+
+def test_fp64_instruction_count_matches_its_profile():
+    """The FP64 sweep's ALU roofline multiplies MFLUP/s by the FP64 pipe
+    instructions per fluid cell that ncu counted on the current kernel; the
+    benchmark's constant and the committed profile summary must agree."""
+    import re
+    import bench
+    path = os.path.join(os.path.dirname(os.path.dirname(__file__)), "profiles", "dense_aa_f64_duct128_ncu.md")
+    with open(path) as fh:
+        m = re.search(r"Current kernel: (\d+) FP64 pipe instructions per fluid cell", fh.read())
+    assert m, "profile summary lacks the current instruction count"
+    assert float(m.group(1)) == bench.FP64_INSTR_PER_FLUP
