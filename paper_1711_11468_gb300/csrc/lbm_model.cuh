@@ -13,6 +13,7 @@
 #include <type_traits>
 
 #include "lbm_df32.cuh"
+#include "lbm_df64.cuh"
 #include "lbm_sr.cuh"
 
 namespace lbm {
@@ -59,12 +60,19 @@ enum Flag : uint8_t { kFluid = 0, kSolidFullway = 1, kSolidHalfway = 2 };
 //   a = (1 - w+)/2, b = (1 - w-)/2, wp_w[c] = w+ * w_c, c4[c] = 9/2 w+ w_c,
 //   c3[c] = 3 w- w_c for the weight classes c = 0 (faces), 1 (edges),
 //   fk[k-1] = 3 w_k (c_k . F) the body-force source of direction k (its
-//   opposite gets -fk), rest = 1 - w+, wp_w0 = w+ / 3.
+//   opposite gets -fk), rest = 1 - w+, wp_w0 = w+ / 3;
+//   fw60[a] = F_a / w- times 2^60 rounded to an integer and fw_abs28 =
+//   2 (|F_x| + |F_y| + |F_z|) / w- in units of 2^-28 (rounded up), used by the
+//   grid double-float collision of FP64 storage (lbm_df64.cuh), which folds the
+//   force source into the momentum: 3 w- w_c (c.j) + 3 w_c (c.F) =
+//   c3[c] (c.(j + F / w-)), splitting F / w- on the node's grid like the PDFs.
 template <typename A>
 struct Trt {
   A a, b, rest, wp_w0;
   A wp_w[2], c4[2], c3[2];
   A fk[9];
+  long long fw60[3];
+  uint32_t fw_abs28;
 };
 
 // TRT parameters of the stochastically rounded FP16 format plus its random
@@ -277,6 +285,10 @@ struct Storage<__half> {
   }
 };
 
+#ifndef LBM_F64DF_JOIN1
+#define LBM_F64DF_JOIN1 0x7FC00u
+#endif
+
 template <>
 struct Storage<f64df> {
   using Params = Trt<df32>;
@@ -285,7 +297,11 @@ struct Storage<f64df> {
   static constexpr bool kShifted = true, kIncrement = true;
   __device__ __forceinline__ static Raw load(const f64df* p) { return __ldcs(reinterpret_cast<const double*>(p)); }
   __device__ __forceinline__ static void store(f64df* p, Raw v) { __stcs(reinterpret_cast<double*>(p), v); }
+  // Directions whose increment is joined with one FP64 addition (the rest with
+  // two): balances the FP64 pipe against integer instructions.
+  static constexpr uint32_t kJoin1 = LBM_F64DF_JOIN1;
   __device__ __forceinline__ static void relax(Raw (&f)[Q], const Params& p, uint32_t = 0) {
+    if (dfg::collide_grid<kJoin1>(f, p)) return;   // nodes near equilibrium (lbm_df64.cuh)
     df32 d[Q];
     bool out_of_range = false;
 #pragma unroll
@@ -345,8 +361,20 @@ struct Storage<h16sr> {
     collide<float, true, true>(d, p);
     unsigned long long w[5];
     sr_words(p.base, node, w);
+    // The one-addition form is exact when every value is 0 or at least 2^-14
+    // in magnitude; the general form is exact for all. The choice is made per
+    // warp (a vote), so that it is a uniform branch: a warp takes the general
+    // form only if one of its nodes has a value below 2^-14, which is rare.
+    bool small = false;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = round_half_stochastic(d[i], sr_bits(w, i));
+    for (int i = 0; i < Q; ++i) small |= (fabsf(d[i]) < kSrNormalMin) & (d[i] != 0.0f);
+    if (!__any_sync(__activemask(), small)) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) f[i] = round_half_stochastic_normal(d[i], sr_bits(w, i));
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) f[i] = round_half_stochastic_any(d[i], sr_bits(w, i));
+    }
   }
   __device__ __forceinline__ static Raw unpack(h16sr v) { return __half_as_ushort(v.v); }
   __device__ __forceinline__ static h16sr pack(Raw v) { return h16sr{__ushort_as_half((unsigned short)v)}; }

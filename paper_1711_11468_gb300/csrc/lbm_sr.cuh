@@ -6,13 +6,16 @@
 // survive on average.
 //
 // The format stores d_i 2^14 (kSrScaleLog2): FP16's normal range then covers
-// |d| from 2^-28 to 4, and for a number in that range stochastic rounding of an
-// FP32 value is one integer addition: add 13 random bits to its bit pattern
-// (the 13 bits FP32 keeps below the FP16 spacing) and truncate to FP16. The
-// result is the FP16 neighbour away from zero exactly when the 13 dropped bits
-// plus the draw carry, i.e. with probability (remainder / spacing), without
-// bias. Below 2^-14 (scaled) the addition covers less than one FP16 spacing and
-// the rounding leans towards zero; those values are below 2^-28 unscaled.
+// |d| from 2^-28 to 4. The rule: with q the remainder of |x| in FP16 spacings
+// and r a 13-bit draw, |x| rounds to the FP16 neighbour away from zero iff
+// q + r / 2^13 >= 1, in every binade. For an FP32 value in FP16's normal range
+// that is one integer addition: FP32 keeps exactly 13 bits below the FP16
+// spacing there, so adding r to the bit pattern carries into the FP16 bits iff
+// the rule says "away", and truncation to FP16 finishes the rounding. Below
+// 2^-14 FP16's spacing is fixed (2^-24) and FP32 keeps more than 13 bits below
+// it, so there the value is first cut to a fixed-point count of 2^-37 units
+// (the truncation cannot change the decision: r is an integer), then the draw
+// is added and the carry taken.
 //
 // Random bits: splitmix64 (Steele, Lea and Flood, "Fast splittable
 // pseudorandom number generators", OOPSLA 2014) used as a counter-based
@@ -53,12 +56,37 @@ __device__ __forceinline__ unsigned sr_bits(const unsigned long long (&w)[5], in
   return (j % 2) == 0 ? (half & 0x1FFFu) : (half >> 19);
 }
 
-// FP32 -> FP16 bits, stochastically: the draw is added to the magnitude bits
-// (a carry out of the mantissa moves to the next binade, which is the value
-// the rounding goes up to), then the conversion truncates. Infinities may turn
-// into NaN; finite values beyond the FP16 range saturate at 65504.
-__device__ __forceinline__ unsigned short round_half_stochastic(float x, unsigned r13) {
+constexpr float kSrNormalMin = 6.103515625e-05f;   // 2^-14, FP16's smallest normal number
+
+// FP32 -> FP16 bits, stochastically, for |x| >= 2^-14 (or x = 0): the draw is
+// added to the magnitude bits (a carry out of the mantissa moves to the next
+// binade, which is the value the rounding goes up to), then the conversion
+// truncates. Finite values beyond the FP16 range saturate at 65504; non-finite
+// values are outside the format.
+__device__ __forceinline__ unsigned short round_half_stochastic_normal(float x, unsigned r13) {
   return __half_as_ushort(__float2half_rz(__uint_as_float(__float_as_uint(x) + r13)));
+}
+
+// The same rule for any finite x, by integer arithmetic on the bit pattern.
+// Exponent field E >= 113 (|x| >= 2^-14): re-biasing the exponent (127 -> 15)
+// and dropping the 13 low bits after adding the draw gives the FP16 pattern,
+// saturated at 65504. E < 113: |x| = M 2^(E-150) with M the 24-bit significand,
+// so M >> (113 - E) = floor(|x| 2^37), a count of 1/2^13 FP16 subnormal
+// spacings; adding the draw and dropping 13 bits gives the subnormal count (a
+// count of 1024 is the pattern of 2^-14, the next value up). FP32 subnormals
+// and zero lie below 2^-37 and give 0.
+__device__ __forceinline__ unsigned short round_half_stochastic_any(float x, unsigned r13) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned ab = b & 0x7FFFFFFFu;
+  const unsigned e = ab >> 23;
+  unsigned h;
+  if (e >= 113u) {
+    h = min((ab + r13 - (112u << 23)) >> 13, 0x7BFFu);
+  } else {
+    const unsigned m = (ab & 0x7FFFFFu) | 0x800000u;
+    h = ((m >> min(113u - e, 31u)) + r13) >> 13;
+  }
+  return (unsigned short)(h | ((b >> 16) & 0x8000u));
 }
 
 }  // namespace lbm

@@ -1,6 +1,7 @@
 // Single-lattice sweep kernels: one thread per cell of the full array (rows of
 // x on a 2-D grid) or per node of the fluid list. The per-node bodies live in
 // lbm_sweep.cuh and are shared with the batched kernel.
+#include <cmath>
 #include <mutex>
 #include <type_traits>
 
@@ -27,6 +28,15 @@ Trt<Arith<S>> trt_as(const TrtParams& p) {
   // w[1] = w[0] / 2 exactly, so the edge constants are exactly half the face
   // constants; the FP64 collision relies on it (half_exact)
   for (int k = 0; k < 9; ++k) t.fk[k] = (A)p.fk[k];
+  // F / w- in fixed point for the grid collision of FP64 storage; a force too
+  // large for it (|F / w-| >= 2^-5) gets a budget that keeps that path off
+  double fw_abs = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double fw = p.force[a] / p.omega_m;
+    fw_abs += 2.0 * std::fabs(fw);
+    t.fw60[a] = std::fabs(fw) < 0.03125 ? std::llround(fw * 1152921504606846976.0) : 0;   // 2^60
+  }
+  t.fw_abs28 = fw_abs < 0.0625 ? (uint32_t)std::ceil(fw_abs * 268435456.0) : (1u << 30);   // 2^28
   if (Storage<S>::kIncrement) {
     // return f*_i - f_i: the rest direction and the pair terms lose the f_i itself
     t.a = (A)((1.0 - p.omega_p) * 0.5 - 0.5);

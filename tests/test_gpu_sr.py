@@ -127,6 +127,84 @@ def test_one_step_matches_oracle(lbm, orc, addr, prop, odd, cpt):
     assert n > 0.5 * got.size
 
 
+def band_state(dims, flags, seed):
+    """Deviations on the format's grid with scaled magnitudes 2^-26 .. 2^-13:
+    nearly all FP16 subnormals (below 2^-14, spacing 2^-24), so that the
+    rounding of the collided values happens in the subnormal range. Here the
+    FP32 collision's error (about 2^-22 of the node's largest scaled value,
+    2^-35) is far below the spacing and almost every decision is resolved."""
+    rng = np.random.default_rng(seed)
+    n = 19 * int(np.prod(dims))
+    mag = np.exp2(rng.uniform(-26, -13, n)) * rng.choice([-1.0, 1.0], n)
+    d = mag.astype(np.float16).astype(np.float64).reshape(19, -1) / 2.0 ** 14
+    d[:, flags == 2] = 0.0
+    return d
+
+
+@pytest.mark.parametrize("addr", [0, 1])
+@pytest.mark.parametrize("prop", [0, 1])
+@pytest.mark.parametrize("odd", [False, True])
+def test_one_step_in_the_subnormal_range(lbm, orc, addr, prop, odd):
+    """Collided values below 2^-14 (scaled) round by the same rule as larger
+    ones: bit for bit with the oracle wherever the decision is resolved."""
+    dims = (20, 14, 9)
+    fl = sr_flags(dims, addr == 1, 6)
+    d0 = band_state(dims, fl, 17)
+    w = orc.weights()[:, None]
+    f0 = (w + d0) * (fl != 2)
+    om, lam, F = 1.1, 0.25, (1e-14, 0.0, -2e-14)
+    wm = orc.omega_minus(om, lam)
+    seed, t = 0x5EED5EED, 4242
+    h = make_handle(lbm, dims, fl, addr, prop, om, lam, F, tuning=(128, 1, 0))
+    try:
+        if odd:
+            lbm.lbm_step(h, 1)
+        lbm.lbm_write_pdfs(h, 0, f0)
+        lbm.lbm_set_stochastic_rounding(h, seed, t)
+        lbm.lbm_step(h, 1)
+        got = lbm.lbm_read_pdfs(h, 0)
+    finally:
+        lbm.lbm_destroy(h)
+    node_of = orc.build_list(dims, fl)[1] if addr == 1 else None
+    x = orc.step(dims, fl, om, wm, F, f0) - w
+    band = (np.abs(x) * 2.0 ** 14 < 2.0 ** -14) & (x != 0)
+    band[:, fl == 2] = False
+    assert band.mean() > 0.5
+    n = check_step(orc, got, d0, dims, fl, om, wm, F, seed, t, node_of)
+    assert n > 0.9 * got.size
+
+
+def test_subnormal_range_is_unbiased(lbm, orc):
+    """One step from one state under 48 seeds: in the subnormal range the mean
+    rounding error, in spacings, is zero within its statistical error (a rule
+    that truncated there would sit near -0.5)."""
+    dims = (16, 10, 8)
+    fl = sr_flags(dims, False, 7)
+    d0 = band_state(dims, fl, 19)
+    w = orc.weights()[:, None]
+    f0 = (w + d0) * (fl != 2)
+    om, lam, F = 1.0, 3 / 16, (0.0, 0.0, 0.0)
+    x = orc.step(dims, fl, om, orc.omega_minus(om, lam), F, f0) - w
+    lo, hi = scaled_neighbours(x)
+    band = (np.abs(x) * 2.0 ** 14 < 2.0 ** -14) & (hi > lo)
+    band[:, fl != 0] = False
+    errs = []
+    h = make_handle(lbm, dims, fl, 0, 1, om, lam, F, tuning=(128, 1, 0))
+    try:
+        for s in range(48):
+            lbm.lbm_write_pdfs(h, 0, f0)
+            lbm.lbm_set_stochastic_rounding(h, 1000 + s, 0)
+            lbm.lbm_step(h, 1)
+            got = lbm.lbm_read_pdfs(h, 0) - w
+            errs.append((got - x)[band] / (hi - lo)[band])
+    finally:
+        lbm.lbm_destroy(h)
+    e = np.concatenate(errs)
+    assert e.size > 10000
+    assert np.all(np.abs(e) <= 1.0 + 1e-6)
+    assert abs(e.mean()) < 5 * 0.5 / np.sqrt(e.size) + 2.0 ** -13, e.mean()
+
+
 @pytest.mark.parametrize("prop", [0, 1])
 def test_batch_one_step_matches_oracle(lbm, orc, prop):
     """Lattice l of a batch draws from seed + l."""
