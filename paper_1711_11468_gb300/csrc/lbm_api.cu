@@ -208,6 +208,21 @@ void* state_buffer(lbm_handle h, Lattice& L) {
 }
 
 // RAII device scratch for one call, freed after the stream is drained.
+// Device address of host memory that the GPU reads and writes in place
+// (page-locked: allocated or registered with CUDA), or nullptr for ordinary
+// host memory, which the calls stage through device scratch. Kernels that move
+// a host array straight through the chip-to-chip link skip the copy-engine
+// transfer and the scratch buffer.
+void* mapped_host(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();   // an unknown pointer is ordinary host memory
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 struct Scratch {
   lbm_handle h;
   void* p = nullptr;
@@ -675,12 +690,20 @@ int lbm_init_equilibrium(lbm_handle h, int32_t lattice, const double* rho, const
   Lattice& L = h->lat[lattice];
   if (!L.geometry) return fail(LBM_ERR_STATE, "set the geometry before the initial state");
   const size_t nb = (size_t)L.N * sizeof(double);
-  Scratch r(h, rho ? nb : 0), v(h, u ? 3 * nb : 0);
-  if ((rho && !r.p) || (u && !v.p)) return fail(LBM_ERR_OOM, "scratch allocation failed");
-  if (rho) LBM_CUDA(h, cudaMemcpyAsync(r.p, rho, nb, cudaMemcpyHostToDevice, h->stream), "copy rho");
-  if (u) LBM_CUDA(h, cudaMemcpyAsync(v.p, u, 3 * nb, cudaMemcpyHostToDevice, h->stream), "copy u");
-  LBM_CUDA(h, launch_from_canonical(L.view(), current_layout(h), state_buffer(h, L), nullptr,
-                                    rho ? r.as<double>() : nullptr, u ? v.as<double>() : nullptr, h->stream),
+  const double* rho_in = static_cast<const double*>(mapped_host(rho));
+  const double* u_in = static_cast<const double*>(mapped_host(u));
+  Scratch r(h, rho && !rho_in ? nb : 0), v(h, u && !u_in ? 3 * nb : 0);
+  if ((rho && !rho_in && !r.p) || (u && !u_in && !v.p)) return fail(LBM_ERR_OOM, "scratch allocation failed");
+  if (rho && !rho_in) {
+    LBM_CUDA(h, cudaMemcpyAsync(r.p, rho, nb, cudaMemcpyHostToDevice, h->stream), "copy rho");
+    rho_in = r.as<double>();
+  }
+  if (u && !u_in) {
+    LBM_CUDA(h, cudaMemcpyAsync(v.p, u, 3 * nb, cudaMemcpyHostToDevice, h->stream), "copy u");
+    u_in = v.as<double>();
+  }
+  LBM_CUDA(h, launch_from_canonical(L.view(), current_layout(h), state_buffer(h, L), nullptr, rho_in, u_in,
+                                    h->stream),
            "initial state");
   k_set_sweep<<<1, 1, 0, h->stream>>>(h->d_sweep, h->phase, 0ull);
   LBM_CUDA(h, cudaGetLastError(), "sweep counter");
@@ -696,11 +719,12 @@ int lbm_write_pdfs(lbm_handle h, int32_t lattice, const double* in, size_t in_le
   if (!L.geometry) return fail(LBM_ERR_STATE, "set the geometry before writing PDFs");
   if (!in || in_len < (size_t)Q * L.N) return fail(LBM_ERR_ARG, "input must hold 19*N doubles");
   const size_t nb = (size_t)Q * L.N * sizeof(double);
-  Scratch c(h, nb);
-  if (!c.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
-  LBM_CUDA(h, cudaMemcpyAsync(c.p, in, nb, cudaMemcpyHostToDevice, h->stream), "copy pdfs");
-  LBM_CUDA(h, launch_from_canonical(L.view(), current_layout(h), state_buffer(h, L), c.as<double>(), nullptr,
-                                    nullptr, h->stream),
+  const double* direct = static_cast<const double*>(mapped_host(in));
+  Scratch c(h, direct ? 0 : nb);
+  if (!direct && !c.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
+  if (!direct) LBM_CUDA(h, cudaMemcpyAsync(c.p, in, nb, cudaMemcpyHostToDevice, h->stream), "copy pdfs");
+  LBM_CUDA(h, launch_from_canonical(L.view(), current_layout(h), state_buffer(h, L), direct ? direct : c.as<double>(),
+                                    nullptr, nullptr, h->stream),
            "write state");
   k_set_sweep<<<1, 1, 0, h->stream>>>(h->d_sweep, h->phase, 0ull);
   LBM_CUDA(h, cudaGetLastError(), "sweep counter");
@@ -803,11 +827,13 @@ int lbm_read_pdfs(lbm_handle h, int32_t lattice, double* out, size_t out_len) {
   Lattice& L = h->lat[lattice];
   if (!out || out_len < (size_t)Q * L.N) return fail(LBM_ERR_ARG, "output must hold 19*N doubles");
   const size_t nb = (size_t)Q * L.N * sizeof(double);
-  Scratch c(h, nb);
-  if (!c.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
-  LBM_CUDA(h, launch_to_canonical(L.view(), current_layout(h), state_buffer(h, L), c.as<double>(), h->stream),
+  double* direct = static_cast<double*>(mapped_host(out));
+  Scratch c(h, direct ? 0 : nb);
+  if (!direct && !c.p) return fail(LBM_ERR_OOM, "scratch allocation failed");
+  LBM_CUDA(h, launch_to_canonical(L.view(), current_layout(h), state_buffer(h, L), direct ? direct : c.as<double>(),
+                                  h->stream),
            "read state");
-  LBM_CUDA(h, cudaMemcpyAsync(out, c.p, nb, cudaMemcpyDeviceToHost, h->stream), "copy pdfs");
+  if (!direct) LBM_CUDA(h, cudaMemcpyAsync(out, c.p, nb, cudaMemcpyDeviceToHost, h->stream), "copy pdfs");
   LBM_CUDA(h, cudaStreamSynchronize(h->stream), "read sync");
   return check_device_status(h);
 }
@@ -816,13 +842,16 @@ int lbm_read_macroscopic(lbm_handle h, int32_t lattice, double* rho, double* u) 
   if (int rc = need_state(h, lattice)) return rc;
   Lattice& L = h->lat[lattice];
   const size_t nb = (size_t)L.N * sizeof(double);
-  Scratch r(h, rho ? nb : 0), v(h, u ? 3 * nb : 0);
-  if ((rho && !r.p) || (u && !v.p)) return fail(LBM_ERR_OOM, "scratch allocation failed");
+  double* rho_out = static_cast<double*>(mapped_host(rho));
+  double* u_out = static_cast<double*>(mapped_host(u));
+  Scratch r(h, rho && !rho_out ? nb : 0), v(h, u && !u_out ? 3 * nb : 0);
+  if ((rho && !rho_out && !r.p) || (u && !u_out && !v.p)) return fail(LBM_ERR_OOM, "scratch allocation failed");
   LBM_CUDA(h, launch_macroscopic(L.view(), current_layout(h), state_buffer(h, L), L.trt.force,
-                                 rho ? r.as<double>() : nullptr, u ? v.as<double>() : nullptr, h->stream),
+                                 rho ? (rho_out ? rho_out : r.as<double>()) : nullptr,
+                                 u ? (u_out ? u_out : v.as<double>()) : nullptr, h->stream),
            "macroscopic");
-  if (rho) LBM_CUDA(h, cudaMemcpyAsync(rho, r.p, nb, cudaMemcpyDeviceToHost, h->stream), "copy rho");
-  if (u) LBM_CUDA(h, cudaMemcpyAsync(u, v.p, 3 * nb, cudaMemcpyDeviceToHost, h->stream), "copy u");
+  if (rho && !rho_out) LBM_CUDA(h, cudaMemcpyAsync(rho, r.p, nb, cudaMemcpyDeviceToHost, h->stream), "copy rho");
+  if (u && !u_out) LBM_CUDA(h, cudaMemcpyAsync(u, v.p, 3 * nb, cudaMemcpyDeviceToHost, h->stream), "copy u");
   LBM_CUDA(h, cudaStreamSynchronize(h->stream), "macroscopic sync");
   return check_device_status(h);
 }
