@@ -37,11 +37,12 @@ DIMS = WORKLOAD["dims"]
 # fluid cell; profiles/dense_aa_f64_duct128_ncu.md, whose figure a CPU test keeps
 # equal to this one), the nominal FP64 pipe rate of GB300 (2 per clock per SM at
 # 2.07 GHz; the roofline's peak is the live probe's measured rate), and the DRAM
-# bytes one launch of that sweep moves on the 256^3 duct (dram__bytes_read +
-# write of an even and an odd launch at full size, averaged).
+# bytes one launch of that sweep moves on the 256^3 duct: dram__bytes_read + write
+# of an even and an odd launch on the 160^3 duct (ncu), 300.6 B per fluid node,
+# scaled to the 16,516,096 fluid nodes of the 256^3 duct.
 FP64_INSTR_PER_FLUP = 119.0
 FP64_INSTR_PER_SEC_NOMINAL = 152 * 2 * 2.07e9
-F64_AA_TRAFFIC_PER_LAUNCH = (2.527e9 + 2.449e9 + 2.704e9 + 2.490e9) / 2
+F64_AA_TRAFFIC_PER_LAUNCH = round((1157.4e6 + 1243.8e6) / 2 / 3994240 * 16516096, -6)
 GOLDEN_CHANNEL384 = os.path.join(ROOT, "tests", "golden", "channel384_oracle_profile.txt")
 
 METRIC = "MFLUP/s and % of HBM roofline, FP64 vs FP32/FP16-shifted vs batched, at stated error"

@@ -158,30 +158,15 @@ __device__ __forceinline__ dd cdot_dd(int k, dd x, dd y, dd z) {
 // Returns false, leaving f untouched, when the node is outside the path's
 // range (see the top of the file). kJoin1 has bit i set for the directions
 // whose increment is joined with one FP64 addition (join1), clear for two (join2).
-template <uint32_t kJoin1, typename P>
-__device__ __forceinline__ bool collide_grid(double (&f)[19], const P& p) {
-  // Deviations in fixed point: D_i = (f_i - w_i) 2^60 as a 64-bit integer. For
-  // f_i in [2^-8, 1) (FP64 exponent field 1015..1022) this is the 53-bit
-  // significand shifted left by e - 1015 <= 7 bits, minus w_i 2^60 rounded:
-  // exact up to that rounding (2^-61).
-  uint32_t Dh[19], Dl[19];
-  bool ok = true;
-  uint32_t dabs = 0;   // sum |D_i| in units of 2^-28 (rounded down)
-#pragma unroll
-  for (int i = 0; i < 19; ++i) {
-    const uint32_t hw = (uint32_t)__double2hiint(f[i]), lw = (uint32_t)__double2loint(f[i]);
-    ok &= (hw - (1015u << 20)) < (8u << 20);   // positive, exponent field 1015..1022
-    const uint32_t sh = (hw >> 20) - 1015u;
-    const uint32_t mh = (hw & 0xFFFFFu) | 0x100000u;
-    const uint32_t fh = __funnelshift_l(lw, mh, sh), fl = lw << sh;
-    const int c = i == 0 ? 0 : (((i - 1) % 9) < 3 ? 1 : 2);
-    const unsigned long long W = wfix(c);
-    const unsigned long long Dv = (((unsigned long long)fh << 32) | fl) - W;
-    Dh[i] = (uint32_t)(Dv >> 32);
-    Dl[i] = (uint32_t)Dv;
-    dabs += min((uint32_t)abs((int32_t)Dh[i]), 1u << 24);   // saturated: no overflow
-  }
-  if (!ok) return false;
+// The grid collision's core: from the fixed-point deviations D_i = Dh:Dl
+// (units of 2^-60) and the bound dabs on sum |D_i| (units of 2^-28), the
+// increment f*_i - f_i of every direction as a pair, handed to join(i, x) as
+// soon as it is known. a_inc = -w+/2, b_inc = -w-/2 and rest_inc = -w+ are the
+// increment constants. Returns false, calling no join, if the deviations are too
+// large for an exact grid.
+template <typename P, typename Join>
+__device__ __forceinline__ bool grid_increments(const uint32_t (&Dh)[19], const uint32_t (&Dl)[19], uint32_t dabs,
+                                                const P& p, df32 a_inc, df32 b_inc, df32 rest_inc, Join&& join) {
   // The grid of the high parts: 2^-(28 + k) with the largest k <= 8 for which
   // every partial sum of high parts (edges count one pair twice; the folded
   // force adds 2 |F / w-|_1) stays below 2^24 grid units, i.e. is exact in FP32.
@@ -241,20 +226,47 @@ __device__ __forceinline__ bool collide_grid(double (&f)[19], const P& p) {
            gz = {jz.h + fwk[2].h, jz.l + fwk[2].l};
 
   {
-    const dd inc = add(mul(p.rest, {H[0], L[0]}), mul(p.wp_w0, base));
-    f[0] = (kJoin1 & 1u) ? join1(f[0], inc) : join2(f[0], inc);
+    join(0, add(mul(rest_inc, {H[0], L[0]}), mul(p.wp_w0, base)));
   }
 #pragma unroll
   for (int k = 1; k <= 9; ++k) {
     const int c = k <= 3 ? 0 : 1;
     const dd cj = cdot_dd(k, jx, jy, jz), cg = cdot_dd(k, gx, gy, gz);
-    const dd mU = add(add(mul(p.a, {sH[k], sL[k]}), G[c]), mul(R4[c], sqr(cj)));
-    const dd mV = add(mul(p.b, {aH[k], aL[k]}), mul(c3[c], cg));
-    const dd d1 = add(mU, mV), d2 = add(mU, neg(mV));
-    f[k] = (kJoin1 >> k & 1u) ? join1(f[k], d1) : join2(f[k], d1);
-    f[k + 9] = (kJoin1 >> (k + 9) & 1u) ? join1(f[k + 9], d2) : join2(f[k + 9], d2);
+    const dd mU = add(add(mul(a_inc, {sH[k], sL[k]}), G[c]), mul(R4[c], sqr(cj)));
+    const dd mV = add(mul(b_inc, {aH[k], aL[k]}), mul(c3[c], cg));
+    join(k, add(mU, mV));
+    join(k + 9, add(mU, neg(mV)));
   }
   return true;
+}
+
+template <uint32_t kJoin1, typename P>
+__device__ __forceinline__ bool collide_grid(double (&f)[19], const P& p) {
+  // Deviations in fixed point: D_i = (f_i - w_i) 2^60 as a 64-bit integer. For
+  // f_i in [2^-8, 1) (FP64 exponent field 1015..1022) this is the 53-bit
+  // significand shifted left by e - 1015 <= 7 bits, minus w_i 2^60 rounded:
+  // exact up to that rounding (2^-61).
+  uint32_t Dh[19], Dl[19];
+  bool ok = true;
+  uint32_t dabs = 0;   // sum |D_i| in units of 2^-28 (rounded down)
+#pragma unroll
+  for (int i = 0; i < 19; ++i) {
+    const uint32_t hw = (uint32_t)__double2hiint(f[i]), lw = (uint32_t)__double2loint(f[i]);
+    ok &= (hw - (1015u << 20)) < (8u << 20);   // positive, exponent field 1015..1022
+    const uint32_t sh = (hw >> 20) - 1015u;
+    const uint32_t mh = (hw & 0xFFFFFu) | 0x100000u;
+    const uint32_t fh = __funnelshift_l(lw, mh, sh), fl = lw << sh;
+    const int c = i == 0 ? 0 : (((i - 1) % 9) < 3 ? 1 : 2);
+    const unsigned long long W = wfix(c);
+    const unsigned long long Dv = (((unsigned long long)fh << 32) | fl) - W;
+    Dh[i] = (uint32_t)(Dv >> 32);
+    Dl[i] = (uint32_t)Dv;
+    dabs += min((uint32_t)abs((int32_t)Dh[i]), 1u << 24);   // saturated: no overflow
+  }
+  if (!ok) return false;
+  return grid_increments(Dh, Dl, dabs, p, p.a, p.b, p.rest, [&](int i, dd x) {
+    f[i] = (kJoin1 >> i & 1u) ? join1(f[i], x) : join2(f[i], x);
+  });
 }
 
 }  // namespace dfg
