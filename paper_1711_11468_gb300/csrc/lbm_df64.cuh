@@ -87,9 +87,18 @@ __device__ __forceinline__ dd sqr(dd x) {
 __device__ __forceinline__ dd scale(dd x, float s) { return {x.h * s, x.l * s}; }
 
 // ---------------------------------------------------------------- join
-// f + (h + l) with two FP64 additions of the exactly converted parts.
+// FP32 -> FP64 by integer operations for a value added to f >= 2^-8 (all PDFs
+// on this path): normal numbers convert exactly; zero and FP32 subnormals come
+// out as magnitudes below 2^-125, which the addition to f absorbs exactly, so
+// the conversion needs no test for them.
+__device__ __forceinline__ double f32_to_f64_added(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const uint32_t hw = (((b & 0x7FFFFFFFu) >> 3) + (896u << 20)) | (b & 0x80000000u);
+  return __hiloint2double((int)hw, (int)(b << 29));
+}
+// f + (h + l) with two FP64 additions of the converted parts.
 __device__ __forceinline__ double join2(double f, dd x) {
-  return (f + f32_to_f64(x.h)) + f32_to_f64(x.l);
+  return (f + f32_to_f64_added(x.h)) + f32_to_f64_added(x.l);
 }
 
 // h + l as one FP64 value, by integer operations, for |l| <= ulp(h)/2 (a
@@ -252,8 +261,8 @@ __device__ __forceinline__ bool collide_grid(double (&f)[19], const P& p) {
 #pragma unroll
   for (int i = 0; i < 19; ++i) {
     const uint32_t hw = (uint32_t)__double2hiint(f[i]), lw = (uint32_t)__double2loint(f[i]);
-    ok &= (hw - (1015u << 20)) < (8u << 20);   // positive, exponent field 1015..1022
     const uint32_t sh = (hw >> 20) - 1015u;
+    ok &= sh < 8u;   // positive, exponent field 1015..1022
     const uint32_t mh = (hw & 0xFFFFFu) | 0x100000u;
     const uint32_t fh = __funnelshift_l(lw, mh, sh), fl = lw << sh;
     const int c = i == 0 ? 0 : (((i - 1) % 9) < 3 ? 1 : 2);

@@ -361,14 +361,16 @@ struct Storage<h16sr> {
     collide<float, true, true>(d, p);
     unsigned long long w[5];
     sr_words(p.base, node, w);
-    // The one-addition form is exact when every value is 0 or at least 2^-14
-    // in magnitude; the general form is exact for all. The choice is made per
-    // warp (a vote), so that it is a uniform branch: a warp takes the general
-    // form only if one of its nodes has a value below 2^-14, which is rare.
-    bool small = false;
+    // The one-addition form is exact when every value is at least 2^-14 in
+    // magnitude (or 0); the general form is exact for all and gives the same
+    // bits wherever the first one is exact. The choice is made per warp (a
+    // vote), so that it is a uniform branch: a warp takes the general form only
+    // if one of its nodes has a value below 2^-14 (zeros included, which only
+    // the rest state has), which is rare in a flow.
+    float small = fabsf(d[0]);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) small |= (fabsf(d[i]) < kSrNormalMin) & (d[i] != 0.0f);
-    if (!__any_sync(__activemask(), small)) {
+    for (int i = 1; i < Q; ++i) small = fminf(small, fabsf(d[i]));
+    if (!__any_sync(__activemask(), small < kSrNormalMin)) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) f[i] = round_half_stochastic_normal(d[i], sr_bits(w, i));
     } else {
