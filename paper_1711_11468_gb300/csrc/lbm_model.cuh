@@ -286,7 +286,7 @@ struct Storage<__half> {
 };
 
 #ifndef LBM_F64DF_JOIN1
-#define LBM_F64DF_JOIN1 0x7FC00u
+#define LBM_F64DF_JOIN1 0x7FE7Eu
 #endif
 
 template <>
