@@ -102,26 +102,28 @@ __device__ __forceinline__ double join2(double f, dd x) {
 }
 
 // h + l as one FP64 value, by integer operations, for |l| <= ulp(h)/2 (a
-// FastTwoSum result) and h normal or zero. h's FP64 pattern has 29 zero bits
-// below its FP32 mantissa; l, at most half a unit of h's last FP32 bit, lies
-// within them: its 24-bit significand shifted to h's FP64 spacing (bits below
-// that spacing are dropped, an error below 2^-52 |h|) is added to or, for
-// opposite signs, subtracted from the 64-bit pattern. A subtraction borrows
-// across the binade boundary only when h is a power of two, where the spacing
-// below is half as large: the amount is doubled there.
+// FastTwoSum result) and h normal. h's FP64 pattern has 29 zero bits below its
+// FP32 mantissa; l, at most half a unit of h's last FP32 bit, lies within
+// them: its 24-bit significand shifted to h's FP64 spacing (bits below that
+// spacing are dropped, an error below 2^-52 |h|) is added to or, for opposite
+// signs, subtracted from the 64-bit pattern. A subtraction borrows across the
+// binade boundary only when h is a power of two, where the spacing below is
+// half as large: the amount is doubled there. The value is only ever added to
+// a PDF of at least 2^-8, so zero or subnormal parts need no test: they yield
+// magnitudes below 2^-66 (h zero: about 2^-127; l zero: nothing, or an amount
+// below h's last bit when |h| < 2^-66), which that addition absorbs exactly.
 __device__ __forceinline__ double pair_to_f64(dd x) {
   const uint32_t hb = __float_as_uint(x.h), lb = __float_as_uint(x.l);
   const uint32_t ah = hb & 0x7FFFFFFFu;
-  uint32_t hw = ((ah >> 3) + (896u << 20)) | (hb & 0x80000000u);
-  hw = ah != 0u ? hw : 0u;
+  const uint32_t hw = ((ah >> 3) + (896u << 20)) | (hb & 0x80000000u);
   const uint32_t lw = hb << 29;
-  const int sh = (int)((lb >> 23) & 0xFFu) - (int)(ah >> 23) + 29;
+  const int sh = (int)((lb << 1) >> 24) - (int)(ah >> 23) + 29;
   const uint32_t ml = (lb & 0x7FFFFFu) | 0x800000u;
   uint32_t t;
   // clamped shifts: amounts of 32 or more give 0
   asm("shl.b32 %0, %1, %2;" : "=r"(t) : "r"(ml), "r"((uint32_t)max(sh, 0)));
   asm("shr.b32 %0, %0, %1;" : "+r"(t) : "r"((uint32_t)max(-sh, 0)));
-  const bool opposite = (int32_t)(hb ^ lb) < 0 && (lb & 0x7FFFFFFFu) != 0u;
+  const bool opposite = (int32_t)(hb ^ lb) < 0;
   if (opposite && (hb & 0x7FFFFFu) == 0u) t <<= 1;
   unsigned long long p = ((unsigned long long)hw << 32) | lw;
   p = opposite ? p - t : p + t;
