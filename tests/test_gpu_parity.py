@@ -371,3 +371,35 @@ def test_two_cells_per_thread_bitwise(lbm, orc, prec, prop, nx, halfway):
             lbm.lbm_destroy(h)
     for k in range(1, len(outs)):
         assert np.array_equal(outs[0], outs[k]), k
+
+
+def test_f64_double_float_both_collision_paths(lbm, orc):
+    """FP64 storage with the double-float collision takes the grid path at nodes
+    near equilibrium and the general path elsewhere (a PDF below 2^-8, or
+    deviations too large for the exact grid). One lattice with both kinds of
+    node: one step against the oracle at the FP64 bar, and the same bits in
+    every launch shape and for AA and pull (the choice depends on a node's own
+    values only)."""
+    rng = np.random.default_rng(123)
+    dims = (26, 12, 9)
+    N = int(np.prod(dims))
+    fl = np.zeros(N, dtype=np.uint8)
+    rho = 1.0 + 0.002 * (rng.random(N) - 0.5)
+    u = 0.004 * (rng.random((3, N)) - 0.5)
+    big = rng.random(N) < 0.4                     # general path: |u| ~ 0.2
+    u[:, big] = 0.2 * (rng.random((3, int(big.sum()))) - 0.5)
+    f0 = orc.init_equilibrium(dims, fl, rho, u)
+    tiny = rng.random(N) < 0.05                   # general path: one PDF below 2^-8
+    f0[13, tiny] = 0.003
+    om, F = 1.25, (2e-6, -1e-6, 0.0)
+    ref = orc.step(dims, fl, om, orc.omega_minus(om, LAM), F, f0)
+    outs = []
+    for prop in (0, 1):
+        for threads in (64, 256):
+            out = gpu_run(lbm, dims, flags=fl, prec=3, prop=prop, omega=om, F=F, f0=f0, steps=1, threads=threads)
+            # the general path splits each PDF into FP32 parts with the low 29 bits
+            # rounded to 24: 2^-48 of f_0 ~ 1/3 is 1.2e-15, times omega+ = 1.25
+            assert np.abs(out["pdfs"] - ref).max() <= 4e-15
+            outs.append(out["pdfs"])
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
