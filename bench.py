@@ -408,6 +408,30 @@ def microbench(lbm, stream, elem: int = 8, n: int = 1 << 24, reps: int = 5):
     return out
 
 
+def targets_status(f64_mflups, f64_hbm_frac, variants, accuracy384):
+    """The workload's targets beside what this run measured: FP64 PDFs on the
+    dense duct at >= 80 % of the HBM roofline (by the plain FP64 sweep, bound
+    by the FP64 pipe, and by FP64 storage with the double-float collision), and
+    FP32-/FP16-shifted storage and the batch beating the plain FP64 sweep, with
+    the 384^3 accuracy of the FP32 formats against their 1e-5 target."""
+    if not variants:
+        return {}
+    out = {"f64_dense_hbm_frac_target": 0.8, "f64_arithmetic_hbm_frac": f64_hbm_frac}
+    df = variants.get("f64_double_float_aa", {})
+    if df:
+        out["f64_storage_double_float_hbm_frac"] = df.get("roofline_frac")
+    for name in ("f32_shifted_aa", "f16_shifted_aa", "f32_shifted_double_float_aa", "f16_shifted_stochastic_aa",
+                 "f32_batched_512"):
+        v = variants.get(name, {})
+        if v.get("mflups"):
+            out[name + "_speedup_over_f64"] = round(v["mflups"] / f64_mflups, 2)
+    for name in ("f32_shifted", "f32_shifted_double_float"):
+        e = accuracy384.get(name, {}).get("max_rel_vs_oracle")
+        if e is not None:
+            out[name + "_meets_1e-5"] = bool(e <= 1e-5)
+    return out
+
+
 def fp64_pipe_rate(lbm, stream, iterations: int = 8192, reps: int = 5) -> float:
     """FP64 pipe throughput in G FP64 instructions per second: one full wave of
     resident CTAs, each thread running 16 independent chains of fused
@@ -710,6 +734,7 @@ def run_gpu(args):
             "variants": variants,
             "accuracy_poiseuille64_max_rel": accuracy,
             "accuracy_channel384": accuracy384,
+            "targets": targets_status(value / world, hbm["frac"], variants, accuracy384),
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

@@ -121,3 +121,18 @@ def test_fp64_instruction_count_matches_its_profile():
         m = re.search(r"Current kernel: (\d+) FP64 pipe instructions per fluid cell", fh.read())
     assert m, "profile summary lacks the current instruction count"
     assert float(m.group(1)) == bench.FP64_INSTR_PER_FLUP
+
+
+def test_targets_summary():
+    """The bench line's targets object reports the measured fractions and
+    speed-ups beside the workload's targets, from the variants it timed."""
+    import bench
+    v = {"f64_double_float_aa": {"roofline_frac": 0.66, "mflups": 14600.0},
+         "f32_shifted_aa": {"mflups": 43000.0}, "f32_batched_512": {"mflups": 33000.0}}
+    a = {"f32_shifted": {"max_rel_vs_oracle": 4e-5}, "f32_shifted_double_float": {"max_rel_vs_oracle": 3e-6}}
+    t = bench.targets_status(4400.0, 0.2, v, a)
+    assert t["f64_dense_hbm_frac_target"] == 0.8 and t["f64_arithmetic_hbm_frac"] == 0.2
+    assert t["f64_storage_double_float_hbm_frac"] == 0.66
+    assert t["f32_shifted_aa_speedup_over_f64"] == round(43000.0 / 4400.0, 2)
+    assert t["f32_shifted_meets_1e-5"] is False and t["f32_shifted_double_float_meets_1e-5"] is True
+    assert bench.targets_status(4400.0, 0.2, {}, {}) == {}
