@@ -377,7 +377,8 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_list_staged(const S* __re
   __shared__ int abort_flag;
   const int T = blockDim.x;
   const int j = threadIdx.x;
-  uint32_t* buf[2] = {reinterpret_cast<uint32_t*>(smem), reinterpret_cast<uint32_t*>(smem) + 18 * T};
+  // buffer b at buf0 + b * 18 T (no arrays indexed by b: they would live in local memory)
+  uint32_t* const buf0 = reinterpret_cast<uint32_t*>(smem);
   const int64_t ntiles = (nf + T - 1) / T;
   if (j == 0) {
     mbar_init(&bar[0], 1);
@@ -391,49 +392,77 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_list_staged(const S* __re
     const int64_t first = tile * T;
     const int64_t count = nf - first < T ? nf - first : T;
     const uint32_t row = (uint32_t)((count * 4 + 15) & ~(int64_t)15);
+    uint32_t* buf = buf0 + b * 18 * T;
     mbar_arrive_expect_tx(&bar[b], 18u * row);
-    for (int i = 0; i < 18; ++i) bulk_copy_g2s(buf[b] + i * T, link + (int64_t)i * stride + first, row, &bar[b]);
+    for (int i = 0; i < 18; ++i) bulk_copy_g2s(buf + i * T, link + (int64_t)i * stride + first, row, &bar[b]);
   };
-  uint32_t parity[2] = {0u, 0u};
-  bool pending[2] = {false, false};   // thread 0's view of copies in flight
-  int it = 0;
   int64_t t = blockIdx.x;
-  if (j == 0 && t < ntiles) {
-    issue(t, 0);
-    pending[0] = true;
-  }
-  for (; t < ntiles; t += gridDim.x, ++it) {
+  if (j == 0 && t < ntiles) issue(t, 0);
+  // pass `it` uses buffer it & 1 in its ((it >> 1) + 1)-th fill: phase parity (it >> 1) & 1
+  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
     const int b = it & 1;
     const int64_t tn = t + gridDim.x;
     if (j == 0 && tn < ntiles) {
-      fence_proxy_async_smem();   // the reads of buf[b^1] (previous tile) are ordered before its refill
+      fence_proxy_async_smem();   // the reads of buffer b^1 (previous tile) are ordered before its refill
       issue(tn, b ^ 1);
-      pending[b ^ 1] = true;
     }
-    const bool ok = mbar_wait_bounded(&bar[b], parity[b]);
-    if (ok) {
-      parity[b] ^= 1u;
-      if (j == 0) pending[b] = false;
-    }
-    if (!ok) {
+    if (!mbar_wait_bounded(&bar[b], (uint32_t)(it >> 1) & 1u)) {
       atomicOr(status, kStatusWaitTimeout);
       abort_flag = 1;
     } else {
       const int64_t k = t * T + j;
       if (k < nf) {
         if (KIND == kPull)
-          pull_list_node_staged<S>(src, dst, buf[b], T, j, k, stride, p);
+          pull_list_node_staged<S>(src, dst, buf0 + b * 18 * T, T, j, k, stride, p);
         else
-          aa_odd_list_node_staged<S>(dst, buf[b], T, j, k, p);
+          aa_odd_list_node_staged<S>(dst, buf0 + b * 18 * T, T, j, k, p);
       }
     }
     __syncthreads();
-    if (abort_flag) break;
+    if (abort_flag) {
+      // never leave a copy in flight into shared memory that is about to be
+      // released: this tile's and, when issued, the next one's
+      if (j == 0) {
+        mbar_wait_bounded(&bar[b], (uint32_t)(it >> 1) & 1u);
+        if (tn < ntiles) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)((it + 1) >> 1) & 1u);
+      }
+      return;
+    }
   }
-  // never leave a copy in flight into shared memory that is about to be released
-  if (j == 0)
-    for (int b = 0; b < 2; ++b)
-      if (pending[b] && !mbar_wait_bounded(&bar[b], parity[b])) atomicOr(status, kStatusWaitTimeout);
+}
+
+// One node of a run-indexed list sweep: lane `lane` of a 32-node chunk decodes
+// its 18 links from the chunk's headers `hd` and pool slice `pl` (pool index
+// `pb` at pl[0]; le = the mask of lanes 0..lane), then gathers, collides and
+// stores (pull: into dst's own slots; odd AA step: scattered in place).
+template <typename S, int KIND>
+__device__ __forceinline__ void ria_node(const S* __restrict__ src, S* __restrict__ dst, const uint2* hd,
+                                         const uint32_t* pl, uint32_t pb, unsigned le, int lane, int64_t k,
+                                         int64_t stride, const ParamsT<S>& p) {
+  uint32_t off[Q];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const uint2 h = hd[i - 1];
+    const unsigned below = h.x & le;
+    off[i] = pl[h.y - pb + (uint32_t)__popc(below) - 1u] + (uint32_t)(lane - 31 + __clz(below));
+  }
+  RawT<S> f[Q];
+  if (KIND == kPull) {
+    f[0] = Storage<S>::load(src + k);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) f[i] = Storage<S>::load(src + off[i]);
+    Storage<S>::relax(f, p, (uint32_t)k);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + k, f[i]);
+  } else {
+    f[0] = Storage<S>::load(dst + k);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) f[i] = Storage<S>::load(dst + off[i]);
+    Storage<S>::relax(f, p, (uint32_t)k);
+    Storage<S>::store(dst + k, f[0]);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) Storage<S>::store(dst + off[opp(i)], f[i]);
+  }
 }
 
 // The same persistent, double-buffered sweep reading the run-indexed code of
@@ -460,9 +489,10 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_list_staged_ria(const S* 
   __shared__ int abort_flag;
   const int T = blockDim.x, C = T / 32;
   const int j = threadIdx.x, lane = j & 31, w = j >> 5;
-  uint2* shead[2] = {reinterpret_cast<uint2*>(smem), reinterpret_cast<uint2*>(smem) + (Q - 1) * C};
-  uint32_t* spool0 = reinterpret_cast<uint32_t*>(shead[1] + (Q - 1) * C);
-  uint32_t* spool[2] = {spool0, spool0 + (Q - 1) * T + 8};
+  // buffer b: headers at shead0 + b 18 C, pool slice at spool0 + b (18 T + 8) words (no arrays
+  // indexed by b: they would live in local memory)
+  uint2* const shead0 = reinterpret_cast<uint2*>(smem);
+  uint32_t* const spool0 = reinterpret_cast<uint32_t*>(shead0 + 2 * (Q - 1) * C);
   const int64_t chunks = (nf + 31) / 32;
   const int64_t ntiles = (nf + T - 1) / T;
   if (j == 0) {
@@ -480,72 +510,142 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_list_staged_ria(const S* 
     const uint32_t pbytes = (a1 - a0) * (uint32_t)sizeof(uint32_t);
     pool_base[b] = a0;
     mbar_arrive_expect_tx(&bar[b], hbytes + pbytes);
-    bulk_copy_g2s(shead[b], head + c0 * (Q - 1), hbytes, &bar[b]);
-    bulk_copy_g2s(spool[b], pool + a0, pbytes, &bar[b]);
+    bulk_copy_g2s(shead0 + b * (Q - 1) * C, head + c0 * (Q - 1), hbytes, &bar[b]);
+    bulk_copy_g2s(spool0 + b * ((Q - 1) * T + 8), pool + a0, pbytes, &bar[b]);
   };
   const unsigned le = (2u << lane) - 1u;   // lanes 0..lane
-  uint32_t parity[2] = {0u, 0u};
-  bool pending[2] = {false, false};
-  int it = 0;
   int64_t t = blockIdx.x;
-  if (j == 0 && t < ntiles) {
-    issue(t, 0);
-    pending[0] = true;
-  }
-  for (; t < ntiles; t += gridDim.x, ++it) {
+  if (j == 0 && t < ntiles) issue(t, 0);
+  // pass `it` uses buffer it & 1 in its ((it >> 1) + 1)-th fill: phase parity (it >> 1) & 1
+  for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
     const int b = it & 1;
     const int64_t tn = t + gridDim.x;
     if (j == 0 && tn < ntiles) {
       fence_proxy_async_smem();
       issue(tn, b ^ 1);
-      pending[b ^ 1] = true;
     }
-    const bool ok = mbar_wait_bounded(&bar[b], parity[b]);
-    if (ok) {
-      parity[b] ^= 1u;
-      if (j == 0) pending[b] = false;
-    }
-    if (!ok) {
+    if (!mbar_wait_bounded(&bar[b], (uint32_t)(it >> 1) & 1u)) {
       atomicOr(status, kStatusWaitTimeout);
       abort_flag = 1;
     } else {
       const int64_t k = t * T + j;
-      if (k < nf) {
-        const uint2* hd = shead[b] + w * (Q - 1);
-        const uint32_t* pl = spool[b];
-        const uint32_t pb = pool_base[b];
-        uint32_t off[Q];
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-          const uint2 h = hd[i - 1];
-          const unsigned below = h.x & le;
-          off[i] = pl[h.y - pb + (uint32_t)__popc(below) - 1u] + (uint32_t)(lane - 31 + __clz(below));
-        }
-        RawT<S> f[Q];
-        if (KIND == kPull) {
-          f[0] = Storage<S>::load(src + k);
-#pragma unroll
-          for (int i = 1; i < Q; ++i) f[i] = Storage<S>::load(src + off[i]);
-          Storage<S>::relax(f, p, (uint32_t)k);
-#pragma unroll
-          for (int i = 0; i < Q; ++i) Storage<S>::store(dir(dst, i, stride) + k, f[i]);
-        } else {
-          f[0] = Storage<S>::load(dst + k);
-#pragma unroll
-          for (int i = 1; i < Q; ++i) f[i] = Storage<S>::load(dst + off[i]);
-          Storage<S>::relax(f, p, (uint32_t)k);
-          Storage<S>::store(dst + k, f[0]);
-#pragma unroll
-          for (int i = 1; i < Q; ++i) Storage<S>::store(dst + off[opp(i)], f[i]);
-        }
-      }
+      if (k < nf)
+        ria_node<S, KIND>(src, dst, shead0 + b * (Q - 1) * C + w * (Q - 1), spool0 + b * ((Q - 1) * T + 8),
+                          pool_base[b], le, lane, k, stride, p);
     }
     __syncthreads();
-    if (abort_flag) break;
+    if (abort_flag) {
+      // never leave a copy in flight into shared memory that is about to be
+      // released: this tile's and, when issued, the next one's
+      if (j == 0) {
+        mbar_wait_bounded(&bar[b], (uint32_t)(it >> 1) & 1u);
+        if (tn < ntiles) mbar_wait_bounded(&bar[b ^ 1], (uint32_t)((it + 1) >> 1) & 1u);
+      }
+      return;
+    }
   }
-  if (j == 0)
-    for (int b = 0; b < 2; ++b)
-      if (pending[b] && !mbar_wait_bounded(&bar[b], parity[b])) atomicOr(status, kStatusWaitTimeout);
+}
+
+// The run-indexed sweep with one pipeline per warp. The tiled kernels above
+// synchronise the whole CTA once per tile before the next bulk copy may
+// overwrite a buffer, so a warp whose gathers have returned waits for the
+// slowest warp of its CTA. Here every warp strides over 32-node chunks on its
+// own (chunk = global warp index + n x warps in the grid), and no warp waits
+// for another. Per warp one staging buffer -- the chunk's 18 headers (144
+// bytes) and its pool slice, rounded out to 16-byte boundaries (at most 18 x
+// 32 + 6 words) -- and one table of decoded links, in which each lane writes
+// and reads only its own column. The lanes decode chunk c from the staging
+// buffer into the table; then lane 0 starts chunk c + step's copy into the
+// staging buffer, which lands while the warp gathers, collides and scatters
+// chunk c from the table. The node body is the link-table one, so the 18
+// offsets need no registers across the collision (58-66 registers instead of
+// 80-108 for FP16, FP32 and FP64). Results equal the other list kernels' bit
+// for bit. (The same per-warp pipeline over the link table, 18 bulk copies
+// of 128 bytes per chunk, was slower than the tiled kernel and is not built.)
+constexpr size_t kWarpLinkBytes = (size_t)(Q - 1) * 32 * sizeof(uint32_t);   // 2304: the decoded table
+constexpr int kWarpPoolWords = (Q - 1) * 32 + 8;
+constexpr size_t kWarpStageBytes = (Q - 1) * sizeof(uint2) + kWarpPoolWords * sizeof(uint32_t);   // 2480
+static_assert(kWarpStageBytes % 16 == 0, "bulk-copy destinations stay 16-byte aligned");
+constexpr size_t kWarpRiaBytes = kWarpStageBytes + kWarpLinkBytes;   // 4784
+constexpr size_t warp_ria_smem_bytes(int threads) { return (size_t)(threads / 32) * kWarpRiaBytes; }
+
+template <typename S, int KIND>
+__global__ void __launch_bounds__(kStagedMaxThreads) k_list_warp_ria(const S* __restrict__ src, S* __restrict__ dst,
+                                                                     const uint2* __restrict__ head,
+                                                                     const uint32_t* __restrict__ pool,
+                                                                     const uint32_t* __restrict__ chunk_start,
+                                                                     int64_t nf, int64_t stride, ParamsT<S> lp,
+                                                                     int* status) {
+  const ParamsT<S> p = begin_sweep<S>(lp);
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bars[kStagedMaxThreads / 32];
+  __shared__ uint32_t pool_base[kStagedMaxThreads / 32];   // pool index at the staged slice's first word
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint2* hd = reinterpret_cast<uint2*>(smem + (size_t)w * kWarpRiaBytes);
+  uint32_t* pl = reinterpret_cast<uint32_t*>(hd + (Q - 1));
+  uint32_t* table = reinterpret_cast<uint32_t*>(smem + (size_t)w * kWarpRiaBytes + kWarpStageBytes);
+  uint64_t* bar = &bars[w];
+  const int chunks = (int)((nf + 31) / 32);   // links are 32-bit element offsets: 19 nf < 2^32
+  const int step = (int)(gridDim.x * (blockDim.x >> 5));
+  auto issue = [&](int c) {   // lane 0
+    const uint32_t a0 = chunk_start[c] & ~3u, a1 = (chunk_start[c + 1] + 3u) & ~3u;
+    pool_base[w] = a0;
+    const uint32_t pbytes = (a1 - a0) * (uint32_t)sizeof(uint32_t);
+    mbar_arrive_expect_tx(bar, (uint32_t)((Q - 1) * sizeof(uint2)) + pbytes);
+    bulk_copy_g2s(hd, head + (int64_t)c * (Q - 1), (uint32_t)((Q - 1) * sizeof(uint2)), bar);
+    bulk_copy_g2s(pl, pool + a0, pbytes, bar);
+  };
+  int c = (int)(blockIdx.x * (blockDim.x >> 5)) + w;
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    if (c < chunks) issue(c);
+  }
+  __syncwarp();
+  const unsigned le = (2u << lane) - 1u;
+  for (uint32_t parity = 0; c < chunks; c += step, parity ^= 1u) {
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, parity))) {
+      // never leave a copy in flight into shared memory that is about to be released
+      if (lane == 0) {
+        atomicOr(status, kStatusWaitTimeout);
+        mbar_wait_bounded(bar, parity);
+      }
+      return;
+    }
+    const int64_t k = (int64_t)c * 32 + lane;
+    if (k < nf) {
+      const uint32_t pb = pool_base[w];
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const uint2 h = hd[i - 1];
+        const unsigned below = h.x & le;
+        table[(i - 1) * 32 + lane] = pl[h.y - pb + (uint32_t)__popc(below) - 1u] + (uint32_t)(lane - 31 + __clz(below));
+      }
+    }
+    __syncwarp();   // every lane's reads of the staging buffer (and of pool_base) come before its refill
+    if (lane == 0 && c + step < chunks) {
+      fence_proxy_async_smem();
+      issue(c + step);
+    }
+    if (k < nf) {
+      if (KIND == kPull)
+        pull_list_node_staged<S>(src, dst, table, 32, lane, k, stride, p);
+      else
+        aa_odd_list_node_staged<S>(dst, table, 32, lane, k, p);
+    }
+  }
+}
+
+template <typename K>
+int warp_pipeline_grid(K kernel, int threads, size_t smem_bytes, size_t smem_max, int64_t nf) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem_bytes);
+  const int64_t g = (int64_t)std::max(1, sms) * std::max(1, per_sm);
+  const int64_t warps = (nf + 31) / 32, need = (warps + threads / 32 - 1) / (threads / 32);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, need));
 }
 
 template <typename S, int KIND>
@@ -650,16 +750,21 @@ cudaError_t sweep_typed(const LatticeView& v, SweepKind kind, int parity, const 
   } else {
     if (v.n_nodes == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((v.n_nodes + threads - 1) / threads);
-    const int64_t ntiles = blocks;
+    const size_t ria_smem = warp_ria_smem_bytes(threads), ria_max = warp_ria_smem_bytes(kStagedMaxThreads);
     const bool ria = v.status && v.ria_head && v.ria_pool && v.ria_chunk_start;
     switch (kind) {
       case kPull:
-        if (ria)
-          k_list_staged_ria<S, kPull><<<staged_ria_grid<S, kPull>(threads, ntiles), threads,
+        if (ria && v.ria_per_warp)
+          k_list_warp_ria<S, kPull><<<warp_pipeline_grid(k_list_warp_ria<S, kPull>, threads, ria_smem, ria_max,
+                                                         v.n_nodes),
+                                      threads, ria_smem, s>>>(src, dst, v.ria_head, v.ria_pool, v.ria_chunk_start,
+                                                              v.n_nodes, v.stride, p, v.status);
+        else if (ria)
+          k_list_staged_ria<S, kPull><<<staged_ria_grid<S, kPull>(threads, blocks), threads,
                                          staged_ria_smem_bytes(threads), s>>>(
               src, dst, v.ria_head, v.ria_pool, v.ria_chunk_start, v.n_nodes, v.stride, p, v.status);
         else if (v.status)
-          k_list_staged<S, kPull><<<staged_grid<S, kPull>(threads, ntiles), threads, staged_smem_bytes(threads), s>>>(
+          k_list_staged<S, kPull><<<staged_grid<S, kPull>(threads, blocks), threads, staged_smem_bytes(threads), s>>>(
               src, dst, v.link, v.n_nodes, v.stride, p, v.status);
         else
           k_list_pull<S><<<blocks, threads, 0, s>>>(src, dst, v.link, v.n_nodes, v.stride, p);
@@ -668,12 +773,17 @@ cudaError_t sweep_typed(const LatticeView& v, SweepKind kind, int parity, const 
         k_list_aa_even<S><<<blocks, threads, 0, s>>>(dst, v.n_nodes, v.stride, p);
         break;
       case kAAOdd:
-        if (ria)
-          k_list_staged_ria<S, kAAOdd><<<staged_ria_grid<S, kAAOdd>(threads, ntiles), threads,
+        if (ria && v.ria_per_warp)
+          k_list_warp_ria<S, kAAOdd><<<warp_pipeline_grid(k_list_warp_ria<S, kAAOdd>, threads, ria_smem, ria_max,
+                                                          v.n_nodes),
+                                       threads, ria_smem, s>>>(nullptr, dst, v.ria_head, v.ria_pool,
+                                                               v.ria_chunk_start, v.n_nodes, v.stride, p, v.status);
+        else if (ria)
+          k_list_staged_ria<S, kAAOdd><<<staged_ria_grid<S, kAAOdd>(threads, blocks), threads,
                                           staged_ria_smem_bytes(threads), s>>>(
               nullptr, dst, v.ria_head, v.ria_pool, v.ria_chunk_start, v.n_nodes, v.stride, p, v.status);
         else if (v.status)
-          k_list_staged<S, kAAOdd><<<staged_grid<S, kAAOdd>(threads, ntiles), threads, staged_smem_bytes(threads),
+          k_list_staged<S, kAAOdd><<<staged_grid<S, kAAOdd>(threads, blocks), threads, staged_smem_bytes(threads),
                                       s>>>(nullptr, dst, v.link, v.n_nodes, v.stride, p, v.status);
         else
           k_list_aa_odd<S><<<blocks, threads, 0, s>>>(dst, v.link, v.n_nodes, v.stride, p);
