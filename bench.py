@@ -211,10 +211,8 @@ def make_porous(lbm, stream, precision, propagation, pack):
 
 def porous_variant(lbm, stream, precision, propagation, steps, pack, peak):
     """The porous medium on a fluid list, autotuned (block size and link
-    encoding: the table, or the run-indexed code staged per CTA tile or per
-    warp), then timed with the link table and with the run-indexed code
-    (reduced indirect addressing) at the chosen block size: the chosen
-    run-indexed mode, or the per-warp one when the table won."""
+    encoding), then timed with the link table and with the run-indexed code
+    (reduced indirect addressing) at the chosen block size."""
     h = make_porous(lbm, stream, precision, propagation, pack)
     timed = {}
     try:
@@ -222,11 +220,10 @@ def porous_variant(lbm, stream, precision, propagation, steps, pack, peak):
         table_bytes, ria_bytes = lbm.lbm_adjacency_bytes(h, 0)
         lbm.lbm_autotune(h, 4)
         chosen = lbm.lbm_get_run_indexing(h)
-        ria_mode = chosen if chosen != lbm.LBM_LINK_TABLE else lbm.LBM_RUN_INDEXED_WARP
-        for mode in (chosen, lbm.LBM_LINK_TABLE if chosen != lbm.LBM_LINK_TABLE else ria_mode):
-            lbm.lbm_set_run_indexing(h, mode)
+        for ria in (chosen, not chosen):
+            lbm.lbm_set_run_indexing(h, ria)
             lbm.lbm_step(h, 4)
-            timed[mode != lbm.LBM_LINK_TABLE] = time_steps(lbm, h, steps, stream)
+            timed[ria] = time_steps(lbm, h, steps, stream)
         lbm.lbm_set_run_indexing(h, chosen)
         tuning = lbm.lbm_get_tuning(h)
     finally:
@@ -245,13 +242,9 @@ def porous_variant(lbm, stream, precision, propagation, steps, pack, peak):
         out["run_indexed" if ria else "link_table"] = {
             "mflups": round(mflups, 1), "bytes_per_flup": round(bpf[ria], 1), "achieved_gbs": round(gbs, 1),
             "roofline_frac": round(gbs / peak, 4)}
-    out["run_indexed"]["staging"] = {lbm.LBM_RUN_INDEXED_CTA: "per CTA tile",
-                                     lbm.LBM_RUN_INDEXED_WARP: "per warp"}[ria_mode]
-    best = out["run_indexed" if chosen != lbm.LBM_LINK_TABLE else "link_table"]
-    mode_name = {lbm.LBM_LINK_TABLE: "link table", lbm.LBM_RUN_INDEXED_CTA: "run-indexed, staged per CTA tile",
-                 lbm.LBM_RUN_INDEXED_WARP: "run-indexed, staged per warp"}[chosen]
+    best = out["run_indexed" if chosen else "link_table"]
     return {"mflups": best["mflups"], "bytes_per_flup": best["bytes_per_flup"], "achieved_gbs": best["achieved_gbs"],
-            "roofline_frac": best["roofline_frac"], "autotuned": {"threads": tuning[0], "links": mode_name},
+            "roofline_frac": best["roofline_frac"], "autotuned": {"threads": tuning[0], "run_indexing": chosen},
             "by_encoding": out, "steps": steps, "fluid_cells": nf,
             "porosity": round(nf / float(np.prod(inputs.POROUS_256["dims"])), 4),
             "workload": "porous 256^3, spheres r 4-12, fluid list + int32 adjacency, half-way bounce-back"}
@@ -582,8 +575,7 @@ def run_sweep_only(args):
     if args.tuning:
         lbm.lbm_set_tuning(h, *[int(v) for v in args.tuning.split(",")])
     if args.run_indexing:
-        lbm.lbm_set_run_indexing(h, {"off": lbm.LBM_LINK_TABLE, "cta": lbm.LBM_RUN_INDEXED_CTA,
-                                     "on": lbm.LBM_RUN_INDEXED_WARP}[args.run_indexing])
+        lbm.lbm_set_run_indexing(h, args.run_indexing == "on")
     if args.steps_per_pass:
         lbm.lbm_set_temporal_blocking(h, args.steps_per_pass)
     lbm.lbm_step(h, args.warmup)
@@ -822,9 +814,8 @@ def main():
     ap.add_argument("--tuning", default="", help="profiling: threads,cells_per_thread,ctas_per_sm")
     ap.add_argument("--steps-per-pass", type=int, default=0, choices=[0, 1, 2],
                     help="profiling: temporal blocking of full-array pull sweeps (2 = two steps per launch)")
-    ap.add_argument("--run-indexing", default="", choices=["", "on", "cta", "off"],
-                    help="profiling: fluid lists read the run-indexed links staged per warp (on) or per CTA "
-                         "tile (cta), or the link table (off)")
+    ap.add_argument("--run-indexing", default="", choices=["", "on", "off"],
+                    help="profiling: fluid lists read the run-indexed links (on) or the link table (off)")
     args = ap.parse_args()
     if args.config >= 0:
         args.sweep_only = True

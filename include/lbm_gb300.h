@@ -219,20 +219,14 @@ int lbm_get_temporal_blocking(lbm_handle h, int32_t* steps_per_pass);
  * need no lookup of their own). For indirectly addressed lattices the library
  * keeps, next to the link table, a code per chunk of 32 consecutive list nodes
  * and direction: a mask of the nodes that start a run of consecutive links,
- * and the first link of each run. `mode` selects what the single-lattice list
- * sweeps (pull, and the odd AA step) read:
- *   LBM_LINK_TABLE (0)        the link table, staged per CTA tile;
- *   LBM_RUN_INDEXED_CTA (1)   the code, staged per CTA tile (one CTA-wide
- *                             barrier per tile; the default);
- *   LBM_RUN_INDEXED_WARP (2)  the code, staged per warp and decoded into a
- *                             per-warp link table (no CTA-wide barrier).
- * Results are identical in every mode. The batched sweep always reads the
- * table. lbm_autotune tries all three. The code is built and checked against
- * the table when the geometry is set; it costs 144 bytes per 32 nodes plus 4
- * bytes per run. LBM_ERR_ARG unless mode is 0, 1 or 2. */
-enum lbm_run_indexing { LBM_LINK_TABLE = 0, LBM_RUN_INDEXED_CTA = 1, LBM_RUN_INDEXED_WARP = 2 };
-int lbm_set_run_indexing(lbm_handle h, int32_t mode);
-int lbm_get_run_indexing(lbm_handle h, int32_t* mode);
+ * and the first link of each run. With enable = 1 (the default) the
+ * single-lattice list sweeps (pull, and the odd AA step) read the code instead
+ * of the table; results are identical either way. The batched sweep always
+ * reads the table. lbm_autotune tries both. The code is built and checked
+ * against the table when the geometry is set; it costs 144 bytes per 32 nodes
+ * plus 4 bytes per run. LBM_ERR_ARG unless enable is 0 or 1. */
+int lbm_set_run_indexing(lbm_handle h, int32_t enable);
+int lbm_get_run_indexing(lbm_handle h, int32_t* enabled);
 
 /* Index bytes one sweep over lattice `lattice` reads per full pass over its
  * nodes: out[0] for the link table (18 x 4 bytes per fluid node), out[1] for

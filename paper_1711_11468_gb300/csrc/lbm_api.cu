@@ -81,9 +81,7 @@ struct lbm_lattice_s {
   int phase = 0;         // total steps mod 2: AA parity, pull buffer holding the state
   bool poisoned = false;
   int threads = 256, cells_per_thread = 1, ctas_per_sm = 0;
-  // list sweeps: 0 read the link table; 1 the run-indexed code, staged per CTA;
-  // 2 the run-indexed code, staged per warp
-  int run_indexing = 1;
+  bool run_indexing = true;   // staged list sweeps read the run-indexed links
   int steps_per_pass = 1;     // 2: temporal blocking (single full-array pull lattice)
   bool two_step() const {
     return steps_per_pass == 2 && lat.size() == 1 && prop == LBM_PULL_TWO_GRID && !lat[0].indirect();
@@ -437,7 +435,7 @@ int ready_to_step(lbm_handle h) {
 // Autotuner results for the process, keyed by tune_signature().
 struct TuneChoice {
   int threads, cells_per_thread, ctas_per_sm;
-  int run_indexing;
+  bool run_indexing;
   int steps_per_pass;
 };
 std::mutex g_tune_mu;
@@ -476,7 +474,6 @@ LatticeView sweep_view(lbm_handle h, size_t k) {
     v.ria_head = h->lat[k].ria_head;
     v.ria_pool = h->lat[k].ria_pool;
     v.ria_chunk_start = h->lat[k].ria_chunk_start;
-    v.ria_per_warp = h->run_indexing == 2;
   }
   v.sr_seed = h->sr_seed + (unsigned long long)k;
   v.sweep_ctr = h->d_sweep;
@@ -762,11 +759,11 @@ int lbm_get_temporal_blocking(lbm_handle h, int32_t* steps_per_pass) {
   return LBM_OK;
 }
 
-int lbm_set_run_indexing(lbm_handle h, int32_t mode) {
+int lbm_set_run_indexing(lbm_handle h, int32_t enable) {
   if (int rc = check_handle(h)) return rc;
-  if (mode < 0 || mode > 2) return fail(LBM_ERR_ARG, "mode must be 0, 1 or 2");
+  if (enable != 0 && enable != 1) return fail(LBM_ERR_ARG, "enable must be 0 or 1");
   h->drop_graphs();
-  h->run_indexing = mode;
+  h->run_indexing = enable != 0;
   return LBM_OK;
 }
 
@@ -784,10 +781,10 @@ int lbm_adjacency_bytes(lbm_handle h, int32_t lattice, int64_t out[2]) {
   return LBM_OK;
 }
 
-int lbm_get_run_indexing(lbm_handle h, int32_t* mode) {
+int lbm_get_run_indexing(lbm_handle h, int32_t* enabled) {
   if (int rc = check_handle(h)) return rc;
-  if (!mode) return fail(LBM_ERR_ARG, "null output");
-  *mode = h->run_indexing;
+  if (!enabled) return fail(LBM_ERR_ARG, "null output");
+  *enabled = h->run_indexing ? 1 : 0;
   return LBM_OK;
 }
 
@@ -994,7 +991,7 @@ int lbm_autotune_save(const char* path) {
                    "steps_per_pass\n");
   for (const auto& kv : g_tune_cache)
     std::fprintf(fp, "%s %d %d %d %d %d\n", kv.first.c_str(), kv.second.threads, kv.second.cells_per_thread,
-                 kv.second.ctas_per_sm, kv.second.run_indexing, kv.second.steps_per_pass);
+                 kv.second.ctas_per_sm, kv.second.run_indexing ? 1 : 0, kv.second.steps_per_pass);
   const bool ok = std::fclose(fp) == 0;
   return ok ? LBM_OK : fail(LBM_ERR_ARG, std::string("cannot write ") + path);
 }
@@ -1012,12 +1009,12 @@ int lbm_autotune_load(const char* path) {
     char sig[8192];
     int t = 0, c = 0, g = 0, r = 0, spp = 0;
     if (std::sscanf(line, "%8191s %d %d %d %d %d", sig, &t, &c, &g, &r, &spp) != 6 || t < 32 || t > 512 ||
-        t % 32 != 0 || (c != 1 && c != 2 && c != 4 && c != 8) || g < 0 || g > 64 || r < 0 || r > 2 ||
+        t % 32 != 0 || (c != 1 && c != 2 && c != 4 && c != 8) || g < 0 || g > 64 || (r != 0 && r != 1) ||
         (spp != 1 && spp != 2)) {
       std::fclose(fp);
       return fail(LBM_ERR_ARG, std::string(path) + ": malformed line " + std::to_string(lineno));
     }
-    read[sig] = TuneChoice{t, c, g, r, spp};
+    read[sig] = TuneChoice{t, c, g, r == 1, spp};
   }
   std::fclose(fp);
   std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -1066,7 +1063,7 @@ int lbm_autotune(lbm_handle h, int32_t steps) {
   }
   struct Shape {
     int threads, cpt, ctas;
-    int ria;   // run-indexing mode
+    bool ria;
     int spp;   // steps per pass
   };
   std::vector<Shape> shapes;
@@ -1078,9 +1075,9 @@ int lbm_autotune(lbm_handle h, int32_t steps) {
     const bool dense = !h->lat[0].indirect();
     for (int t : {64, 128, 192, 256, 384, 512})
       for (int c : {1, 2})
-        for (int r : {2, 1, 0})
-          if ((c == 1 || dense) && (r == 2 || !dense))
-            shapes.push_back({t, c, 0, dense ? h->run_indexing : r, 1});
+        for (int r : {1, 0})
+          if ((c == 1 || dense) && (r == 1 || !dense))
+            shapes.push_back({t, c, 0, dense ? h->run_indexing : r == 1, 1});
     if (dense && h->prop == LBM_PULL_TWO_GRID)   // two steps per pass: one fixed launch shape
       shapes.push_back({h->threads, h->cells_per_thread, 0, h->run_indexing, 2});
   }

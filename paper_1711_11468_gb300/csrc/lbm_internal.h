@@ -52,7 +52,6 @@ struct LatticeView {
   const uint2* ria_head = nullptr;            // [chunks][18] {run-start mask, pool start}
   const uint32_t* ria_pool = nullptr;         // first link of each run
   const uint32_t* ria_chunk_start = nullptr;  // [chunks + 1] pool start of each chunk
-  bool ria_per_warp = false;                  // stage the code per warp (else per CTA tile)
   // FP16 stochastic format only: the lattice's seed and the handle's pair of
   // sweep counters (a sweep of parity q reads word q and writes word q ^ 1).
   unsigned long long sr_seed = 0;

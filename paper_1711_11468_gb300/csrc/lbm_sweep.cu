@@ -255,10 +255,10 @@ __global__ void __launch_bounds__(512) k_dense_aa_odd_pair(S* __restrict__ pdf, 
   if (x >= nx) return;
   const int row = blockIdx.x;
   const int z = row / ny, y = row - z * ny;
-  const int n = x + nx * row;
+  int n = x + nx * row;
   const bool ua = flags[n] == kFluid, ub = flags[n + 1] == kFluid;
   if (!ua && !ub) return;
-  const Nbr na(x, y, z, nx, ny, nz), nb(x + 1, y, z, nx, ny, nz);
+  Nbr na(x, y, z, nx, ny, nz), nb(x + 1, y, z, nx, ny, nz);
   RawT<S> f[Q], g[Q];
   if (!(ua && ub)) {
     if (ua) {
@@ -284,6 +284,8 @@ __global__ void __launch_bounds__(512) k_dense_aa_odd_pair(S* __restrict__ pdf, 
   }
   Storage<S>::relax(f, p, (uint32_t)n);
   Storage<S>::relax(g, p, (uint32_t)(n + 1));
+  opaque<S, false>(na, n);
+  opaque<S, false>(nb, n);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if (cx(i) == 0) {
@@ -546,108 +548,6 @@ __global__ void __launch_bounds__(kStagedMaxThreads) k_list_staged_ria(const S* 
   }
 }
 
-// The run-indexed sweep with one pipeline per warp. The tiled kernels above
-// synchronise the whole CTA once per tile before the next bulk copy may
-// overwrite a buffer, so a warp whose gathers have returned waits for the
-// slowest warp of its CTA. Here every warp strides over 32-node chunks on its
-// own (chunk = global warp index + n x warps in the grid), and no warp waits
-// for another. Per warp one staging buffer -- the chunk's 18 headers (144
-// bytes) and its pool slice, rounded out to 16-byte boundaries (at most 18 x
-// 32 + 6 words) -- and one table of decoded links, in which each lane writes
-// and reads only its own column. The lanes decode chunk c from the staging
-// buffer into the table; then lane 0 starts chunk c + step's copy into the
-// staging buffer, which lands while the warp gathers, collides and scatters
-// chunk c from the table. The node body is the link-table one, so the 18
-// offsets need no registers across the collision (58-66 registers instead of
-// 80-108 for FP16, FP32 and FP64). Results equal the other list kernels' bit
-// for bit. (The same per-warp pipeline over the link table, 18 bulk copies
-// of 128 bytes per chunk, was slower than the tiled kernel and is not built.)
-constexpr size_t kWarpLinkBytes = (size_t)(Q - 1) * 32 * sizeof(uint32_t);   // 2304: the decoded table
-constexpr int kWarpPoolWords = (Q - 1) * 32 + 8;
-constexpr size_t kWarpStageBytes = (Q - 1) * sizeof(uint2) + kWarpPoolWords * sizeof(uint32_t);   // 2480
-static_assert(kWarpStageBytes % 16 == 0, "bulk-copy destinations stay 16-byte aligned");
-constexpr size_t kWarpRiaBytes = kWarpStageBytes + kWarpLinkBytes;   // 4784
-constexpr size_t warp_ria_smem_bytes(int threads) { return (size_t)(threads / 32) * kWarpRiaBytes; }
-
-template <typename S, int KIND>
-__global__ void __launch_bounds__(kStagedMaxThreads) k_list_warp_ria(const S* __restrict__ src, S* __restrict__ dst,
-                                                                     const uint2* __restrict__ head,
-                                                                     const uint32_t* __restrict__ pool,
-                                                                     const uint32_t* __restrict__ chunk_start,
-                                                                     int64_t nf, int64_t stride, ParamsT<S> lp,
-                                                                     int* status) {
-  const ParamsT<S> p = begin_sweep<S>(lp);
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ uint64_t bars[kStagedMaxThreads / 32];
-  __shared__ uint32_t pool_base[kStagedMaxThreads / 32];   // pool index at the staged slice's first word
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint2* hd = reinterpret_cast<uint2*>(smem + (size_t)w * kWarpRiaBytes);
-  uint32_t* pl = reinterpret_cast<uint32_t*>(hd + (Q - 1));
-  uint32_t* table = reinterpret_cast<uint32_t*>(smem + (size_t)w * kWarpRiaBytes + kWarpStageBytes);
-  uint64_t* bar = &bars[w];
-  const int chunks = (int)((nf + 31) / 32);   // links are 32-bit element offsets: 19 nf < 2^32
-  const int step = (int)(gridDim.x * (blockDim.x >> 5));
-  auto issue = [&](int c) {   // lane 0
-    const uint32_t a0 = chunk_start[c] & ~3u, a1 = (chunk_start[c + 1] + 3u) & ~3u;
-    pool_base[w] = a0;
-    const uint32_t pbytes = (a1 - a0) * (uint32_t)sizeof(uint32_t);
-    mbar_arrive_expect_tx(bar, (uint32_t)((Q - 1) * sizeof(uint2)) + pbytes);
-    bulk_copy_g2s(hd, head + (int64_t)c * (Q - 1), (uint32_t)((Q - 1) * sizeof(uint2)), bar);
-    bulk_copy_g2s(pl, pool + a0, pbytes, bar);
-  };
-  int c = (int)(blockIdx.x * (blockDim.x >> 5)) + w;
-  if (lane == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-    if (c < chunks) issue(c);
-  }
-  __syncwarp();
-  const unsigned le = (2u << lane) - 1u;
-  for (uint32_t parity = 0; c < chunks; c += step, parity ^= 1u) {
-    if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, parity))) {
-      // never leave a copy in flight into shared memory that is about to be released
-      if (lane == 0) {
-        atomicOr(status, kStatusWaitTimeout);
-        mbar_wait_bounded(bar, parity);
-      }
-      return;
-    }
-    const int64_t k = (int64_t)c * 32 + lane;
-    if (k < nf) {
-      const uint32_t pb = pool_base[w];
-#pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const uint2 h = hd[i - 1];
-        const unsigned below = h.x & le;
-        table[(i - 1) * 32 + lane] = pl[h.y - pb + (uint32_t)__popc(below) - 1u] + (uint32_t)(lane - 31 + __clz(below));
-      }
-    }
-    __syncwarp();   // every lane's reads of the staging buffer (and of pool_base) come before its refill
-    if (lane == 0 && c + step < chunks) {
-      fence_proxy_async_smem();
-      issue(c + step);
-    }
-    if (k < nf) {
-      if (KIND == kPull)
-        pull_list_node_staged<S>(src, dst, table, 32, lane, k, stride, p);
-      else
-        aa_odd_list_node_staged<S>(dst, table, 32, lane, k, p);
-    }
-  }
-}
-
-template <typename K>
-int warp_pipeline_grid(K kernel, int threads, size_t smem_bytes, size_t smem_max, int64_t nf) {
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem_bytes);
-  const int64_t g = (int64_t)std::max(1, sms) * std::max(1, per_sm);
-  const int64_t warps = (nf + 31) / 32, need = (warps + threads / 32 - 1) / (threads / 32);
-  return (int)std::max<int64_t>(1, std::min<int64_t>(g, need));
-}
-
 template <typename S, int KIND>
 int staged_ria_grid(int threads, int64_t ntiles) {
   static std::once_flag once;
@@ -750,16 +650,10 @@ cudaError_t sweep_typed(const LatticeView& v, SweepKind kind, int parity, const 
   } else {
     if (v.n_nodes == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((v.n_nodes + threads - 1) / threads);
-    const size_t ria_smem = warp_ria_smem_bytes(threads), ria_max = warp_ria_smem_bytes(kStagedMaxThreads);
     const bool ria = v.status && v.ria_head && v.ria_pool && v.ria_chunk_start;
     switch (kind) {
       case kPull:
-        if (ria && v.ria_per_warp)
-          k_list_warp_ria<S, kPull><<<warp_pipeline_grid(k_list_warp_ria<S, kPull>, threads, ria_smem, ria_max,
-                                                         v.n_nodes),
-                                      threads, ria_smem, s>>>(src, dst, v.ria_head, v.ria_pool, v.ria_chunk_start,
-                                                              v.n_nodes, v.stride, p, v.status);
-        else if (ria)
+        if (ria)
           k_list_staged_ria<S, kPull><<<staged_ria_grid<S, kPull>(threads, blocks), threads,
                                          staged_ria_smem_bytes(threads), s>>>(
               src, dst, v.ria_head, v.ria_pool, v.ria_chunk_start, v.n_nodes, v.stride, p, v.status);
@@ -773,12 +667,7 @@ cudaError_t sweep_typed(const LatticeView& v, SweepKind kind, int parity, const 
         k_list_aa_even<S><<<blocks, threads, 0, s>>>(dst, v.n_nodes, v.stride, p);
         break;
       case kAAOdd:
-        if (ria && v.ria_per_warp)
-          k_list_warp_ria<S, kAAOdd><<<warp_pipeline_grid(k_list_warp_ria<S, kAAOdd>, threads, ria_smem, ria_max,
-                                                          v.n_nodes),
-                                       threads, ria_smem, s>>>(nullptr, dst, v.ria_head, v.ria_pool,
-                                                               v.ria_chunk_start, v.n_nodes, v.stride, p, v.status);
-        else if (ria)
+        if (ria)
           k_list_staged_ria<S, kAAOdd><<<staged_ria_grid<S, kAAOdd>(threads, blocks), threads,
                                           staged_ria_smem_bytes(threads), s>>>(
               nullptr, dst, v.ria_head, v.ria_pool, v.ria_chunk_start, v.n_nodes, v.stride, p, v.status);

@@ -77,6 +77,27 @@ struct Nbr {
   __device__ __forceinline__ int down(int i) const { return up(opp(i)); }
 };
 
+// The odd AA step scatters to the 18 addresses its gather read. Passing the
+// node index and the neighbour offsets through an empty asm statement between
+// the two hides that from the compiler, which then recomputes the addresses
+// after the collision (a few integer instructions each) instead of keeping 18
+// 64-bit addresses live across it. Done for the shifted FP32 and FP16 formats,
+// whose sweeps are bound by memory requests in flight: 44-72 instead of 78-123
+// registers, +2% on the 256^3 duct. The double-float collisions are bound by
+// instruction issue and lose more to the extra instructions than they gain;
+// plain FP64 is bound by its FP64 pipe either way. With half-way walls (kHW:
+// the addresses depend on neighbour flags too) it is done for every format:
+// there the FP64 and double-float kernels would otherwise spill 90-290 bytes.
+template <typename S, bool kHW>
+constexpr bool kRecomputeScatter =
+    kHW || std::is_same<S, __half>::value || std::is_same<S, float>::value || std::is_same<S, h16sr>::value;
+
+template <typename S, bool kHW>
+__device__ __forceinline__ void opaque(Nbr& nb, int& n) {
+  if constexpr (kRecomputeScatter<S, kHW>)
+    asm volatile("" : "+r"(n), "+r"(nb.xm), "+r"(nb.xp), "+r"(nb.ym), "+r"(nb.yp), "+r"(nb.zm), "+r"(nb.zp));
+}
+
 template <typename S>
 __device__ __forceinline__ const S* dir(const S* base, int i, int64_t stride) {
   return base + (int64_t)i * stride;
@@ -138,7 +159,7 @@ template <typename S, bool kHW>
 __device__ __forceinline__ void aa_odd_dense_node(S* __restrict__ pdf, const uint8_t* __restrict__ flags, int x,
                                                   int y, int z, int n, int nx, int ny, int nz, int64_t stride,
                                                   const ParamsT<S>& p) {
-  const Nbr nb(x, y, z, nx, ny, nz);
+  Nbr nb(x, y, z, nx, ny, nz);
   RawT<S> f[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -149,6 +170,7 @@ __device__ __forceinline__ void aa_odd_dense_node(S* __restrict__ pdf, const uin
       f[i] = Storage<S>::load(dir(pdf, opp(i), stride) + m);
   }
   Storage<S>::relax(f, p, (uint32_t)n);
+  opaque<S, kHW>(nb, n);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int m = n + nb.down(i);
@@ -193,7 +215,8 @@ __device__ __forceinline__ void aa_odd_dense_gather(const S* __restrict__ pdf, c
 
 template <typename S, bool kHW>
 __device__ __forceinline__ void aa_odd_dense_scatter(S* __restrict__ pdf, const uint8_t* __restrict__ flags,
-                                                     const Nbr& nb, int n, int64_t stride, const RawT<S> (&f)[Q]) {
+                                                     Nbr nb, int n, int64_t stride, const RawT<S> (&f)[Q]) {
+  opaque<S, kHW>(nb, n);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int m = n + nb.down(i);

@@ -19,7 +19,6 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_STATE, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_UNSUPPORT
  LBM_F16_SHIFTED_STOCHASTIC) = range(6)
 LBM_DIRECT, LBM_INDIRECT = 0, 1
 LBM_PULL_TWO_GRID, LBM_AA_INPLACE = 0, 1
-LBM_LINK_TABLE, LBM_RUN_INDEXED_CTA, LBM_RUN_INDEXED_WARP = range(3)
 
 PRECISION = {"f64": LBM_F64, "f32": LBM_F32_SHIFTED, "f16": LBM_F16_SHIFTED, "f64df": LBM_F64_DOUBLE_FLOAT,
              "f32df": LBM_F32_SHIFTED_DOUBLE_FLOAT, "f16sr": LBM_F16_SHIFTED_STOCHASTIC}
@@ -253,9 +252,8 @@ def lbm_get_temporal_blocking(h: Handle) -> int:
     return int(v.value)
 
 
-def lbm_set_run_indexing(h: Handle, mode: int):
-    """mode: LBM_LINK_TABLE, LBM_RUN_INDEXED_CTA or LBM_RUN_INDEXED_WARP."""
-    _check(load().lbm_set_run_indexing(h, int(mode)))
+def lbm_set_run_indexing(h: Handle, enable: bool):
+    _check(load().lbm_set_run_indexing(h, 1 if enable else 0))
 
 
 def lbm_adjacency_bytes(h: Handle, lattice: int = 0):
@@ -265,10 +263,10 @@ def lbm_adjacency_bytes(h: Handle, lattice: int = 0):
     return int(out[0]), int(out[1])
 
 
-def lbm_get_run_indexing(h: Handle) -> int:
+def lbm_get_run_indexing(h: Handle) -> bool:
     v = ctypes.c_int32()
     _check(load().lbm_get_run_indexing(h, ctypes.byref(v)))
-    return int(v.value)
+    return bool(v.value)
 
 
 def lbm_set_stochastic_rounding(h: Handle, seed: int, sweep: int = 0):

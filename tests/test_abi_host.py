@@ -97,33 +97,22 @@ def test_autotune_cache_file_round_trip(lib, tmp_path):
     src = tmp_path / "tune.txt"
     src.write_text("# comment\n"
                    "NVIDIA_GB300/sm152/p1/g1/n1/256x256x256d16516096F 256 2 0 1 1\n"
-                   "NVIDIA_GB300/sm152/p0/g0/n1/64x64x64i200000H 128 1 0 1 2\n"
-                   "NVIDIA_GB300/sm152/p2/g1/n1/256x256x256i9999999H 256 1 0 2 1\n")
+                   "NVIDIA_GB300/sm152/p0/g0/n1/64x64x64i200000H 128 1 0 1 2\n")
     lbm.lbm_autotune_load(str(src))
-    assert lbm.lbm_autotune_cache()[0] == 3
+    assert lbm.lbm_autotune_cache()[0] == 2
     out = tmp_path / "out.txt"
     lbm.lbm_autotune_save(str(out))
     lines = sorted(line for line in out.read_text().splitlines() if not line.startswith("#"))
     assert lines == sorted(line for line in src.read_text().splitlines() if not line.startswith("#"))
-    for line in ("sig 256 3 0 1 1\n", "sig 256 1 0 3 1\n"):   # 3 cells per thread; run-indexing mode 3
-        bad = tmp_path / "bad.txt"
-        bad.write_text(line)
-        with pytest.raises(lbm.LbmError) as e:
-            lbm.lbm_autotune_load(str(bad))
-        assert e.value.code == lbm.LBM_ERR_ARG and "malformed" in str(e.value)
-        assert lbm.lbm_autotune_cache()[0] == 3
+    bad = tmp_path / "bad.txt"
+    bad.write_text("sig 256 3 0 1 1\n")
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_autotune_load(str(bad))
+    assert e.value.code == lbm.LBM_ERR_ARG and "malformed" in str(e.value)
+    assert lbm.lbm_autotune_cache()[0] == 2
     with pytest.raises(lbm.LbmError):
         lbm.lbm_autotune_load(str(tmp_path / "missing.txt"))
     lbm.lbm_autotune_clear()
-
-
-def test_run_indexing_modes_match_header():
-    from paper_1711_11468_gb300 import lbm
-    text = open(HEADER).read()
-    body = re.search(r"enum lbm_run_indexing \{([^}]*)\}", text).group(1)
-    values = {k: int(v) for k, v in re.findall(r"(LBM_\w+) = (\d+)", body)}
-    assert values == {"LBM_LINK_TABLE": lbm.LBM_LINK_TABLE, "LBM_RUN_INDEXED_CTA": lbm.LBM_RUN_INDEXED_CTA,
-                      "LBM_RUN_INDEXED_WARP": lbm.LBM_RUN_INDEXED_WARP}
 
 
 def test_desc_layout_matches_header():

@@ -1,8 +1,7 @@
 """Run-indexed adjacency (RIA) of fluid lists: the staged list sweeps that
-decode their links from the run-length code -- staged per CTA tile or per warp
--- give bit for bit the results of the sweeps that read the link table, for
-pull and AA, on regular and irregular geometries and block sizes, and match
-the FP64 oracle."""
+decode their links from the run-length code give bit for bit the results of the
+sweeps that read the link table, for pull and AA, on regular and irregular
+geometries and block sizes, and match the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -47,18 +46,16 @@ def test_run_index_equals_table_bitwise(lbm, geom, prop, prec):
     dims, fl = GEOM[geom]
     u = inputs.velocity_perturbation(*dims, seed=9, amplitude=0.02, flags=fl)
     for threads in (64, 256):
-        table = run(lbm, dims, fl, prec, prop, 21, threads, lbm.LBM_LINK_TABLE, u)
-        for mode in (lbm.LBM_RUN_INDEXED_CTA, lbm.LBM_RUN_INDEXED_WARP):
-            got = run(lbm, dims, fl, prec, prop, 21, threads, mode, u)
-            assert np.array_equal(got, table), (geom, prop, prec, threads, mode)
+        a = run(lbm, dims, fl, prec, prop, 21, threads, True, u)
+        b = run(lbm, dims, fl, prec, prop, 21, threads, False, u)
+        assert np.array_equal(a, b), (geom, prop, prec, threads)
 
 
-@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("prop", [0, 1])
-def test_run_index_matches_oracle(lbm, orc, prop, mode):
+def test_run_index_matches_oracle(lbm, orc, prop):
     dims, fl = GEOM["ragged"]
     u = inputs.velocity_perturbation(*dims, seed=4, amplitude=0.02, flags=fl)
-    got = run(lbm, dims, fl, 0, prop, 17, 96, mode, u)
+    got = run(lbm, dims, fl, 0, prop, 17, 96, True, u)
     f0 = orc.init_equilibrium(dims, fl, None, u)
     want = orc.run(dims, fl, 1.1, orc.omega_minus(1.1, 0.2), (2e-5, -1e-5, 1e-5), f0, 17)
     assert np.abs(got - want).max() <= 1e-13
@@ -68,11 +65,10 @@ def test_run_index_switch_and_errors(lbm):
     import torch
     h = lbm.lbm_create_lattice(lbm.make_desc((16, 16, 16), 1, lbm.LBM_INDIRECT, 1), torch.cuda.current_stream())
     try:
-        assert lbm.lbm_get_run_indexing(h) == lbm.LBM_RUN_INDEXED_CTA
-        lbm.lbm_set_run_indexing(h, lbm.LBM_LINK_TABLE)
-        assert lbm.lbm_get_run_indexing(h) == lbm.LBM_LINK_TABLE
-        for bad in (3, -1):
-            assert lbm.load().lbm_set_run_indexing(h, bad) == lbm.LBM_ERR_ARG
-        assert lbm.lbm_get_run_indexing(h) == lbm.LBM_LINK_TABLE
+        assert lbm.lbm_get_run_indexing(h) is True
+        lbm.lbm_set_run_indexing(h, False)
+        assert lbm.lbm_get_run_indexing(h) is False
+        assert lbm.load().lbm_set_run_indexing(h, 2) == lbm.LBM_ERR_ARG
+        assert lbm.lbm_get_run_indexing(h) is False
     finally:
         lbm.lbm_destroy(h)
