@@ -103,8 +103,19 @@ __global__ void k_from_canonical(LatticeView v, Layout layout,
   const int64_t k = map.node(n);
   if (k < 0) return;
   if (layout == kCanonical) {
+    if (src.canon) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) dst[(int64_t)i * v.stride + k] = Storage<S>::from_f64(src.at(i, n), i);
+      for (int i = 0; i < Q; ++i) dst[(int64_t)i * v.stride + k] = Storage<S>::from_f64(src.at(i, n), i);
+    } else {
+      // one read of the cell's density and velocity (possibly over the link to
+      // host memory) for all 19 slots
+      const double r = src.rho ? src.rho[n] : 1.0;
+      const double ux = src.u ? src.u[n] : 0.0, uy = src.u ? src.u[src.N + n] : 0.0,
+                   uz = src.u ? src.u[2 * src.N + n] : 0.0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        dst[(int64_t)i * v.stride + k] = Storage<S>::from_f64(equilibrium_f64(i, r, ux, uy, uz, false), i);
+    }
     return;
   }
   const Cell c = cell_coords(v, n);

@@ -426,7 +426,20 @@ __device__ __forceinline__ void begin_two_sweeps<h16sr>(const TrtSr& p, TrtSr& p
 // Equilibrium in FP64, absolute or shifted by w_i (initialisation only).
 __device__ __forceinline__ double equilibrium_f64(int i, double rho, double ux, double uy, double uz,
                                                   bool shifted) {
-  const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+  // c_i.u as the signed sum of the components c_i selects (c has entries -1, 0,
+  // 1): the same value as the dot product (products by +-1 and 0 are exact),
+  // without the multiplications by 0 and additions of 0 that the compiler must
+  // keep (signed zeros), which made initialisation FP64-pipe bound
+  const int a = cx(i), b = cy(i), c = cz(i);
+  const double tx = a > 0 ? ux : -ux, ty = b > 0 ? uy : -uy, tz = c > 0 ? uz : -uz;
+  double cu = 0.0;
+  if (a != 0 && b != 0 && c != 0) cu = tx + ty + tz;
+  else if (a != 0 && b != 0) cu = tx + ty;
+  else if (a != 0 && c != 0) cu = tx + tz;
+  else if (b != 0 && c != 0) cu = ty + tz;
+  else if (a != 0) cu = tx;
+  else if (b != 0) cu = ty;
+  else if (c != 0) cu = tz;
   const double usq = ux * ux + uy * uy + uz * uz;
   const double w = weight(i);
   if (!shifted) return w * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
