@@ -131,6 +131,38 @@ __global__ void k_from_canonical(LatticeView v, Layout layout,
   }
 }
 
+// The equilibrium of rho/u in the pull or AA form, pushed: every storing cell
+// x evaluates its own equilibrium once (one read of its density and velocity,
+// which may sit in host memory) and writes f_i(x) where the layout keeps it --
+// slot i (pull) / opp(i) (AA) of the upstream cell x - c_i, when that cell
+// stores anything -- and, where x + c_i is a half-way solid, the reflected
+// f_opp(i)(x) into its own slot. Each slot is written once, with the values
+// and conversions of k_from_canonical, which instead gathers every slot's value
+// from the downstream cell (19 reads of the inputs per cell).
+template <typename S>
+__global__ void k_equilibrium_push(LatticeView v, Layout layout, S* __restrict__ dst, CanonSource src) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= v.n_cells) return;
+  const NodeMap map{v};
+  const int64_t k = map.node(n);
+  if (k < 0) return;
+  const double r = src.rho ? src.rho[n] : 1.0;
+  const double ux = src.u ? src.u[n] : 0.0, uy = src.u ? src.u[src.N + n] : 0.0,
+               uz = src.u ? src.u[2 * src.N + n] : 0.0;
+  double feq[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) feq[i] = equilibrium_f64(i, r, ux, uy, uz, false);
+  const Cell c = cell_coords(v, n);
+  dst[k] = Storage<S>::from_f64(feq[0], 0);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int slot = layout == kPullForm ? i : opp(i);
+    if (map.halfway(nbr_cell(v, c, i, +1))) dst[(int64_t)slot * v.stride + k] = Storage<S>::from_f64(feq[opp(i)], i);
+    const int64_t ku = map.node(nbr_cell(v, c, i, -1));
+    if (ku >= 0) dst[(int64_t)slot * v.stride + ku] = Storage<S>::from_f64(feq[i], i);
+  }
+}
+
 template <typename S>
 __global__ void k_to_canonical(LatticeView v, Layout layout,
                                const S* __restrict__ src, double* __restrict__ out) {
@@ -304,9 +336,15 @@ unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 cudaError_t launch_from_canonical(const LatticeView& v, Layout layout, void* dst,
                                   const double* canon, const double* rho, const double* u, cudaStream_t s) {
   const CanonSource src{canon, rho, u, v.n_cells};
-  LBM_DISPATCH_PREC(v.prec, S,
-                    k_from_canonical<S><<<blocks_for(v.n_cells, 256), 256, 0, s>>>(v, layout,
-                                                                                   static_cast<S*>(dst), src));
+  if (!canon && layout != kCanonical) {
+    LBM_DISPATCH_PREC(v.prec, S,
+                      k_equilibrium_push<S><<<blocks_for(v.n_cells, 256), 256, 0, s>>>(v, layout,
+                                                                                       static_cast<S*>(dst), src));
+  } else {
+    LBM_DISPATCH_PREC(v.prec, S,
+                      k_from_canonical<S><<<blocks_for(v.n_cells, 256), 256, 0, s>>>(v, layout,
+                                                                                     static_cast<S*>(dst), src));
+  }
   return cudaGetLastError();
 }
 
