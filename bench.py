@@ -383,7 +383,8 @@ def accuracy_poiseuille64(lbm, stream):
 
 
 def microbench(lbm, stream, elem: int = 8, n: int = 1 << 24, reps: int = 5):
-    """copy-19 and update-19 (Sec. 4.1) on 19 arrays of n elements: GB/s."""
+    """copy-19 and update-19 (Sec. 4.1) on 19 arrays of n elements, and the
+    host link's copy bandwidth each way: GB/s."""
     import torch
     stride = n
     a = torch.empty(19 * stride * elem, dtype=torch.uint8, device="cuda")
@@ -405,6 +406,31 @@ def microbench(lbm, stream, elem: int = 8, n: int = 1 << 24, reps: int = 5):
             best = min(best, e0.elapsed_time(e1) / 1e3)
         out[name + "_gbs"] = round(2 * 19 * n * elem / best / 1e9, 1)
     del a, b
+    out.update(host_link(stream))
+    return out
+
+
+def host_link(stream, nbytes: int = 400 << 20, reps: int = 3):
+    """Page-locked host memory <-> HBM by copy-engine transfers: GB/s each way,
+    best of `reps` (the floor under the end-to-end number's uploads and
+    read-backs)."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h.zero_()
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    out = {}
+    with torch.cuda.stream(stream):
+        for name, dst, src in (("h2d_pinned_gbs", d, h), ("d2h_pinned_gbs", h, d)):
+            best = 1e30
+            for _ in range(reps + 1):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                dst.copy_(src, non_blocking=True)
+                e1.record(stream)
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            out[name] = round(nbytes / best / 1e9, 1)
+    del h, d
     return out
 
 
