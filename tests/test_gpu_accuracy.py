@@ -18,7 +18,7 @@ from paper_1711_11468_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 # Max-relative error of the profile against the FP64 oracle, per storage format:
-# (lower, upper) bounds around the values measured on GB300, with the verdict each
+# (lower, upper) bounds around the values measured on GB300, with the outcome each
 # records against the workload's FP32 target of 1e-5.
 #  - FP64 and FP64 storage with the double-float collision: about 1e-10, the random
 #    round-off walk of a profile (u ~ 5e-4) built from PDFs of size ~0.1.
@@ -33,7 +33,7 @@ pytestmark = pytest.mark.gpu
 #    (measured 4.4e-5): the noise of the random rounding averaged over the 384^2
 #    cells of a plane, the level of FP32 storage, at half its bytes.
 BOUNDS = {0: (0.0, 1e-9), 3: (0.0, 1e-9), 1: (1e-5, 8e-5), 4: (0.0, 1e-5), 2: (0.9, 1.1), 5: (0.0, 8e-5)}
-VERDICT = {0: "round-off", 3: "round-off", 1: "misses 1e-5", 4: "meets 1e-5", 2: "stagnates",
+OUTCOME = {0: "round-off", 3: "round-off", 1: "misses 1e-5", 4: "meets 1e-5", 2: "stagnates",
            5: "FP32 level"}
 
 
@@ -101,4 +101,4 @@ def test_channel384_profile_error(lbm, reference, prec):
                        "errors": REPORT}, fh, indent=1)
     assert np.all(np.isfinite(prof))
     lo, hi = BOUNDS[prec]
-    assert lo <= err["max_rel_vs_oracle"] <= hi, (VERDICT[prec], err)
+    assert lo <= err["max_rel_vs_oracle"] <= hi, (OUTCOME[prec], err)
