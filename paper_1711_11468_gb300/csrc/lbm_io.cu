@@ -80,17 +80,14 @@ __device__ void gather_canonical(const LatticeView& v, const NodeMap& map, Layou
 }
 
 // Source of canonical values: a device array [19][N] or the equilibrium of rho/u.
+// (The equilibrium is evaluated per cell by the kernels that take rho/u; at()
+// serves the canonical array.)
 struct CanonSource {
   const double* canon;
   const double* rho;
   const double* u;
   int64_t N;
-  __device__ __forceinline__ double at(int i, int64_t n) const {
-    if (canon) return canon[(int64_t)i * N + n];
-    const double r = rho ? rho[n] : 1.0;
-    const double ux = u ? u[n] : 0.0, uy = u ? u[N + n] : 0.0, uz = u ? u[2 * N + n] : 0.0;
-    return equilibrium_f64(i, r, ux, uy, uz, false);
-  }
+  __device__ __forceinline__ double at(int i, int64_t n) const { return canon[(int64_t)i * N + n]; }
 };
 
 // One thread per cell of the full array; writes the slots of its node.
@@ -112,9 +109,10 @@ __global__ void k_from_canonical(LatticeView v, Layout layout,
       const double r = src.rho ? src.rho[n] : 1.0;
       const double ux = src.u ? src.u[n] : 0.0, uy = src.u ? src.u[src.N + n] : 0.0,
                    uz = src.u ? src.u[2 * src.N + n] : 0.0;
+      double feq[Q];
+      equilibria_f64(r, ux, uy, uz, feq);
 #pragma unroll
-      for (int i = 0; i < Q; ++i)
-        dst[(int64_t)i * v.stride + k] = Storage<S>::from_f64(equilibrium_f64(i, r, ux, uy, uz, false), i);
+      for (int i = 0; i < Q; ++i) dst[(int64_t)i * v.stride + k] = Storage<S>::from_f64(feq[i], i);
     }
     return;
   }
@@ -136,9 +134,9 @@ __global__ void k_from_canonical(LatticeView v, Layout layout,
 // which may sit in host memory) and writes f_i(x) where the layout keeps it --
 // slot i (pull) / opp(i) (AA) of the upstream cell x - c_i, when that cell
 // stores anything -- and, where x + c_i is a half-way solid, the reflected
-// f_opp(i)(x) into its own slot. Each slot is written once, with the values
-// and conversions of k_from_canonical, which instead gathers every slot's value
-// from the downstream cell (19 reads of the inputs per cell).
+// f_opp(i)(x) into its own slot. Each slot is written once. (Gathering each
+// slot's value from its downstream cell instead, as k_from_canonical does for a
+// canonical array, would read every cell's inputs 19 times.)
 template <typename S>
 __global__ void k_equilibrium_push(LatticeView v, Layout layout, S* __restrict__ dst, CanonSource src) {
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -150,8 +148,7 @@ __global__ void k_equilibrium_push(LatticeView v, Layout layout, S* __restrict__
   const double ux = src.u ? src.u[n] : 0.0, uy = src.u ? src.u[src.N + n] : 0.0,
                uz = src.u ? src.u[2 * src.N + n] : 0.0;
   double feq[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) feq[i] = equilibrium_f64(i, r, ux, uy, uz, false);
+  equilibria_f64(r, ux, uy, uz, feq);
   const Cell c = cell_coords(v, n);
   dst[k] = Storage<S>::from_f64(feq[0], 0);
 #pragma unroll

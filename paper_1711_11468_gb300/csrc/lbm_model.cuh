@@ -423,27 +423,34 @@ __device__ __forceinline__ void begin_two_sweeps<h16sr>(const TrtSr& p, TrtSr& p
   pb.base = p.seed + kSplitmixGamma * (1ull + ((t + 1) << 32));
 }
 
-// Equilibrium in FP64, absolute or shifted by w_i (initialisation only).
-__device__ __forceinline__ double equilibrium_f64(int i, double rho, double ux, double uy, double uz,
-                                                  bool shifted) {
-  // c_i.u as the signed sum of the components c_i selects (c has entries -1, 0,
-  // 1): the same value as the dot product (products by +-1 and 0 are exact),
-  // without the multiplications by 0 and additions of 0 that the compiler must
-  // keep (signed zeros), which made initialisation FP64-pipe bound
-  const int a = cx(i), b = cy(i), c = cz(i);
-  const double tx = a > 0 ? ux : -ux, ty = b > 0 ? uy : -uy, tz = c > 0 ? uz : -uz;
-  double cu = 0.0;
-  if (a != 0 && b != 0 && c != 0) cu = tx + ty + tz;
-  else if (a != 0 && b != 0) cu = tx + ty;
-  else if (a != 0 && c != 0) cu = tx + tz;
-  else if (b != 0 && c != 0) cu = ty + tz;
-  else if (a != 0) cu = tx;
-  else if (b != 0) cu = ty;
-  else if (c != 0) cu = tz;
-  const double usq = ux * ux + uy * uy + uz * uz;
-  const double w = weight(i);
-  if (!shifted) return w * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
-  return w * ((rho - 1.0) + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
+// The 19 FP64 equilibria of one cell (initialisation), by opposite pairs: f_k
+// and f_k+9 (c_k+9 = -c_k) share w rho (1 - 3/2 |u|^2 + 9/2 (c.u)^2) and
+// differ in the sign of 3 w rho (c.u), so a pair costs about as much as one
+// direction of the per-direction form below.
+__device__ __forceinline__ void equilibria_f64(double rho, double ux, double uy, double uz, double (&feq)[19]) {
+  const double base = rho * fma(-1.5, fma(ux, ux, fma(uy, uy, uz * uz)), 1.0);
+  feq[0] = (1.0 / 3.0) * base;
+#pragma unroll
+  for (int k = 1; k <= 9; ++k) {
+    const int a = cx(k), b = cy(k), c = cz(k);
+    const double tx = a > 0 ? ux : -ux, ty = b > 0 ? uy : -uy, tz = c > 0 ? uz : -uz;
+    // c_k.u as the signed sum of the components c_k selects: the dot product's
+    // value (products by +-1 and 0 are exact) without the multiplications by 0
+    // and additions of 0 that the compiler must keep (signed zeros)
+    double cu = 0.0;
+    if (a != 0 && b != 0) cu = tx + ty;
+    else if (a != 0 && c != 0) cu = tx + tz;
+    else if (b != 0 && c != 0) cu = ty + tz;
+    else if (a != 0) cu = tx;
+    else if (b != 0) cu = ty;
+    else cu = tz;
+    const double w = weight(k);
+    const double t = rho * cu;
+    const double sym = w * fma(4.5 * t, cu, base);
+    const double anti = (3.0 * w) * t;
+    feq[k] = sym + anti;
+    feq[k + 9] = sym - anti;
+  }
 }
 
 }  // namespace lbm
