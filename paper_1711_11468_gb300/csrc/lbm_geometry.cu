@@ -189,14 +189,48 @@ __global__ void k_face_fluid(const uint8_t* __restrict__ flags, int nx, int ny, 
   if (c) atomicAdd(out + face, c);
 }
 
+// Counts of flag values 0, 1, 2 and anything else into out[0..3]. Four flags
+// per 32-bit load, counters in registers, then a warp sum and one atomic per
+// block and value (blockDim.x a multiple of 32: every lane reaches the sums).
+__device__ __forceinline__ void count_flag(uint32_t f, uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3) {
+  c0 += f == 0u;
+  c1 += f == 1u;
+  c2 += f == 2u;
+  c3 += f > 2u;
+}
+
 __global__ void k_count_flags(const uint8_t* __restrict__ flags, int64_t n, unsigned long long* __restrict__ out) {
-  unsigned long long c[4] = {0, 0, 0, 0};
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-    const uint8_t f = flags[t];
-    c[f < 3 ? f : 3] += 1;
+  uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // bytes before the first 4-byte boundary, whole words, bytes after them
+  const uint32_t mis = (uint32_t)(reinterpret_cast<uintptr_t>(flags) & 3u);
+  const int64_t head = mis ? (n < (int64_t)(4u - mis) ? n : (int64_t)(4u - mis)) : 0;
+  const int64_t words = (n - head) >> 2;
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(flags + head);
+  for (int64_t t = first; t < words; t += stride) {
+    const uint32_t v = w[t];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) count_flag((v >> (8 * b)) & 0xFFu, c0, c1, c2, c3);
   }
-  for (int a = 0; a < 4; ++a)
-    if (c[a]) atomicAdd(out + a, c[a]);
+  const int64_t tail = head + 4 * words;
+  if (first < head) count_flag(flags[first], c0, c1, c2, c3);
+  for (int64_t t = tail + first; t < n; t += stride) count_flag(flags[t], c0, c1, c2, c3);
+  c0 = __reduce_add_sync(0xFFFFFFFFu, c0);
+  c1 = __reduce_add_sync(0xFFFFFFFFu, c1);
+  c2 = __reduce_add_sync(0xFFFFFFFFu, c2);
+  c3 = __reduce_add_sync(0xFFFFFFFFu, c3);
+  __shared__ unsigned long long sum[4];
+  if (threadIdx.x < 4) sum[threadIdx.x] = 0;
+  __syncthreads();
+  if ((threadIdx.x & 31u) == 0) {
+    atomicAdd(&sum[0], (unsigned long long)c0);
+    atomicAdd(&sum[1], (unsigned long long)c1);
+    atomicAdd(&sum[2], (unsigned long long)c2);
+    atomicAdd(&sum[3], (unsigned long long)c3);
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 && sum[threadIdx.x]) atomicAdd(out + threadIdx.x, sum[threadIdx.x]);
 }
 
 }  // namespace
