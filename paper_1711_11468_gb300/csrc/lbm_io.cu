@@ -90,7 +90,9 @@ struct CanonSource {
   __device__ __forceinline__ double at(int i, int64_t n) const { return canon[(int64_t)i * N + n]; }
 };
 
-// One thread per cell of the full array; writes the slots of its node.
+// One thread per cell of the full array; writes the slots of its node from a
+// canonical array, or, in the canonical layout only, from the cell's own
+// equilibrium (the other layouts take rho/u through k_equilibrium_push).
 template <typename S>
 __global__ void k_from_canonical(LatticeView v, Layout layout,
                                  S* __restrict__ dst, CanonSource src) {
